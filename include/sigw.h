@@ -1,0 +1,168 @@
+/*
+ * sigw.h -- C ABI of the GB300 (sm_103a) lattice SIGW library.
+ *
+ * The library evaluates the scalar-induced gravitational-wave spectrum of a
+ * (possibly non-Gaussian) curvature field on a periodic N^3 lattice by the
+ * method of arXiv 2605.27231 (Piccoli, "A Fast Method to Compute Scalar Induced
+ * Gravitational Waves on a Lattice with Primordial Non-Gaussianities"):
+ *
+ *   1. a Gaussian field zeta_g with the log-normal Delta^2_zeta of Eq. eq_lognormal
+ *      (Sec. sec_numerical) is drawn on the lattice;
+ *   2. a pointwise map zeta = F(zeta_g) (local F_NL/G_NL of Sec. "Local
+ *      Non-Gaussianities", or the USR tail -1/3 ln(1-3 zeta_g)) gives
+ *      Phi = 2 zeta / 3 (Sec. sec_sigw);
+ *   3. for each target shell k_c the envelopes A, B of Eq. eq_final_envelopes are
+ *      evaluated as a sum of N_alpha separable FFT convolutions built from the
+ *      eigen-decomposition of the kernels I_s, I_c (Eqs. eq_kernels,
+ *      eq_decomposition, eq_diagonalization, eq_C_matrix_discrete,
+ *      eq_grid_density), projected on the TT polarisations (Sec. sec_sigw);
+ *   4. |A|^2 and |B|^2 are shell-averaged into P_A, P_B and
+ *      Omega(k_c) = k_c^3 / (48 pi^2) sum_l [P_A,l + P_B,l] (Sec. sec_envelope_obs).
+ *
+ * Conventions shared by every entry point
+ *   - N is a power of two, 8 <= N <= 512; L > 0 is the box side; k_f = 2 pi / L.
+ *   - Shells are n_c = 1..N/2 (k_c = n_c k_f), a shell holding the modes with
+ *     |n| in [n_c - 1/2, n_c + 1/2) of the full lattice n in (-N/2, N/2]^3.
+ *   - Every call returns a sigw_status and never aborts the process.  The text
+ *     of the last failure on a plan is kept (sigw_plan_last_error).
+ *   - The library owns all device memory it allocates (cudaMalloc at
+ *     sigw_plan_create, freed by sigw_plan_destroy).  Host arrays passed in are
+ *     owned by the caller and only read or written during the call.
+ *   - A plan is used from one host thread at a time; its work is queued on the
+ *     CUDA stream given at creation (or one it creates).  A server is thread-safe.
+ *   - Arrays indexed [batch][shell] are row-major.
+ */
+#ifndef SIGW_H
+#define SIGW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIGW_ABI_VERSION 1
+
+typedef enum sigw_status {
+  SIGW_OK = 0,
+  SIGW_EINVAL = 1,    /* an argument is out of range or NULL where required */
+  SIGW_ENOMEM = 2,    /* a device or host allocation failed */
+  SIGW_ECUDA = 3,     /* a CUDA runtime call or kernel failed (text in last_error) */
+  SIGW_EDOMAIN = 4,   /* USR map argument 1 - 3 zeta_g fell below the floor (strict mode only) */
+  SIGW_ETIMEOUT = 5,  /* a bounded wait ran out */
+  SIGW_EBUSY = 6,     /* server admission refused: the request does not fit the HBM budget */
+  SIGW_ENOTREADY = 7, /* result not available yet (sigw_poll) */
+  SIGW_ESTATE = 8     /* call out of order (e.g. sigw_spectrum before sigw_generate) */
+} sigw_status;
+
+typedef struct sigw_plan_s* sigw_plan;
+typedef struct sigw_server_s* sigw_server;
+
+/* Log-normal peak of Eq. eq_lognormal: Delta^2(k) = A / sqrt(2 pi sigma^2) exp(-ln^2(k/kstar) / (2 sigma^2)).
+ * kstar is an absolute wave number (units 1/length, same length unit as L). */
+typedef struct sigw_pzeta {
+  double A, sigma, kstar;
+} sigw_pzeta;
+
+typedef enum sigw_mapkind {
+  SIGW_MAP_GAUSS = 0, /* zeta = zeta_g (no FFT round trip) */
+  SIGW_MAP_LOCAL = 1, /* zeta = zeta_g + F_NL (zeta_g^2 - <zeta_g^2>) + G_NL zeta_g^3, <.> the box mean */
+  SIGW_MAP_USR = 2    /* zeta = -1/3 ln(max(1 - 3 zeta_g, usr_floor)); hits below the floor are counted */
+} sigw_mapkind;
+
+/* F_NL is the coefficient of zeta_g^2 (F_NL = 3/5 f_NL). */
+typedef struct sigw_ngmap {
+  int kind;
+  double F_NL, G_NL;
+  double usr_floor; /* > 0; 1e-6 if 0 is given */
+} sigw_ngmap;
+
+/* Plan options.  sigw_opts_default fills the paper's decomposition meta-parameters
+ * (Fig. fig_eigenvalues caption, Sec. sec_numerical): n_modes = 200, n_alpha = 50,
+ * umin = 1e-3, umax = 15, upiv = 1, sigp = 0.5, Ap = 10; precision 32; alpha_batch 0 (auto);
+ * max_batch 1; strict_domain 0. */
+typedef struct sigw_opts {
+  int n_modes;        /* cells of the u-grid (N_modes) */
+  int n_alpha;        /* separable terms kept (N_alpha), 1 <= n_alpha <= n_modes */
+  double umin, umax;  /* u-grid range */
+  double upiv, sigp, Ap; /* grid density bump of Eq. eq_grid_density */
+  int precision;      /* 32: FP32 fields and FFTs (FP64 plan, twiddles and bin sums); 64: FP64 throughout */
+  int alpha_batch;    /* terms per first/second-pass launch; 0 picks a value */
+  int max_batch;      /* most realisations handled by one sigw_generate / sigw_spectrum call */
+  int strict_domain;  /* nonzero: USR floor hits make sigw_generate return SIGW_EDOMAIN */
+} sigw_opts;
+
+/* Fill *o with the defaults above.  Returns SIGW_EINVAL if o is NULL. */
+sigw_status sigw_opts_default(sigw_opts* o);
+
+/* Device memory (bytes) a plan with these arguments allocates.  opts may be NULL (defaults). */
+sigw_status sigw_plan_footprint(int N, const sigw_opts* opts, size_t* bytes);
+
+/* "sigw_plan": build the kernel decomposition (Sec. sec_decomposition: u-grid, C matrices,
+ * Jacobi eigen-decomposition, truncation to n_alpha by |sigma|), the per-shell cell tables,
+ * the FFT twiddles (FP64 generated) and the device buffers for up to opts->max_batch
+ * realisations.  cuda_stream is a cudaStream_t (NULL: the plan creates its own stream).
+ * Errors: SIGW_EINVAL (N not a power of two in [8, 512], L <= 0, bad opts),
+ * SIGW_ENOMEM (device allocation), SIGW_ECUDA. */
+sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_stream, sigw_plan* out);
+sigw_status sigw_plan_destroy(sigw_plan plan);
+const char* sigw_plan_last_error(sigw_plan plan);
+
+/* The truncated separable terms of kernel m (0: I_s / envelope A, 1: I_c / envelope B), Eq. eq_decomposition:
+ * sigma[n_alpha] eigenvalues sorted by |sigma| descending, phi[n_alpha * n_modes] the value of phi_a on
+ * each cell (row-major [a][cell]), edges[n_modes + 1] the cell edges of the u-grid.  Any pointer may be NULL. */
+sigw_status sigw_plan_kernel_terms(sigw_plan plan, int m, double* sigma, double* phi, double* edges);
+
+/* Synthesis (steps 1-2 above) for `batch` realisations, seeds[b] the Philox4x32-10 key of realisation b
+ * (noise g(x) ~ N(0,1) per cell from counter (cell, 0, 0, 0), Box-Muller in FP64).  Leaves Phi~ resident
+ * on the device.  usr_hits (nullable, host, [batch]) receives the USR floor-hit counts.  Waits for the stream.
+ * Errors: SIGW_EINVAL (batch out of [1, max_batch], bad parameters), SIGW_EDOMAIN (strict mode), SIGW_ECUDA. */
+sigw_status sigw_generate(sigw_plan plan, const sigw_pzeta* pz, const sigw_ngmap* map, const uint64_t* seeds,
+                          int batch, int64_t* usr_hits);
+
+/* Envelopes, TT projection and shell binning (steps 3-4) for the realisations of the last sigw_generate.
+ * shells: n_shells shell indices in [1, N/2] (NULL: all N/2 in order).  Host outputs, [batch][n_shells],
+ * any may be NULL: omega (Omega_GW), PA, PB (P_A, P_B summed over polarisations), Nk (modes per shell).
+ * Waits for the stream.  Errors: SIGW_ESTATE (no generated field), SIGW_EINVAL, SIGW_ECUDA. */
+sigw_status sigw_spectrum(sigw_plan plan, const int* shells, int n_shells, double* omega, double* PA, double* PB,
+                          int64_t* Nk);
+
+/* As sigw_spectrum, but only queues the work on the plan's stream and writes device memory:
+ * dev_out (device, [batch][n_shells][4] doubles: P_A, P_B, N_k, Omega).  n_shells <= N/2. */
+sigw_status sigw_spectrum_async(sigw_plan plan, const int* shells, int n_shells, double* dev_out);
+
+/* Copy Phi~ of realisation b to host memory in the standard half-spectrum layout
+ * [k0][k1][k2], k2 = 0..N/2 (N*N*(N/2+1) complex values of the plan precision: float or double pairs),
+ * continuum normalisation X~(k) = dx^3 sum_x X(x) e^{-ik.x}. */
+sigw_status sigw_copy_phi(sigw_plan plan, int b, void* host_out);
+
+/* The library's 3-D real FFT on device buffers of the plan precision (test and utility entry point).
+ * direction -1: real in[N][N][N] -> complex out[N][N][N/2+1] (unnormalised forward DFT);
+ * direction +1: complex in -> real out (unnormalised inverse DFT; in is not modified).  Queued on the
+ * plan's stream; does not wait. */
+sigw_status sigw_fft3d(sigw_plan plan, int direction, const void* in_dev, void* out_dev);
+
+/* Block the calling thread until the plan's stream is idle. */
+sigw_status sigw_synchronize(sigw_plan plan);
+
+/* Human-readable text of a status code. */
+const char* sigw_strerror(sigw_status s);
+
+/* Host-only (no GPU needed): the truncated decomposition a plan with these options uses, for kernel m
+ * (0: I_s, 1: I_c).  Same outputs as sigw_plan_kernel_terms; opts may be NULL (defaults).
+ * Also reports all n_modes eigenvalues (sigma_all[n_modes], sorted by |sigma| descending) when non-NULL. */
+sigw_status sigw_decompose(const sigw_opts* opts, int m, double* sigma, double* phi, double* edges, double* sigma_all);
+
+/* Host-only: the cell table of target shell n_c, lut[msq] for msq = 0..msq_max: the u-grid cell holding
+ * u = sqrt(msq)/n_c, decided on squares ((e_i n_c)^2 <= msq in FP64), or n_modes outside [umin, umax). */
+sigw_status sigw_cell_table(const sigw_opts* opts, int n_c, int msq_max, int16_t* lut);
+
+/* Test hook for failure handling: the next `n`-th device allocation made by the library fails with
+ * SIGW_ENOMEM (n = 1: the next one; n <= 0 disables).  Affects the calling process only. */
+sigw_status sigw_debug_fail_alloc(int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIGW_H */

@@ -1,0 +1,565 @@
+// C ABI of the lattice SIGW library: plan lifetime, device buffers, and the
+// orchestration of the synthesis chain and of the per-shell hot loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sigw.h"
+#include "ops.h"
+#include "plan.h"
+
+namespace {
+
+std::atomic<int> g_fail_alloc{0};
+
+const double kPi = 3.14159265358979323846;
+
+bool is_pow2_in_range(int N) { return N >= 8 && N <= 512 && (N & (N - 1)) == 0; }
+
+sigw::DecompParams params_of(const sigw_opts& o) {
+  sigw::DecompParams p;
+  p.n_modes = o.n_modes;
+  p.n_alpha = o.n_alpha;
+  p.umin = o.umin;
+  p.umax = o.umax;
+  p.upiv = o.upiv;
+  p.sigp = o.sigp;
+  p.Ap = o.Ap;
+  return p;
+}
+
+int auto_alpha_batch(const sigw_opts& o) {
+  if (o.alpha_batch > 0) return std::min(o.alpha_batch, o.n_alpha);
+  return std::min(o.n_alpha, 10);
+}
+
+// Sizes (bytes) of every device buffer of a plan.
+struct Sizes {
+  size_t phi, T, W, synth, F, F2, partial, out, lut, tab, tw, amp, rows_sq;
+  int maxblk;
+  size_t total() const { return phi + T + std::max(W, synth) + F + F2 + partial + out + lut + tab + tw + amp + rows_sq + 4096; }
+};
+
+Sizes sizes_of(int N, const sigw_opts& o) {
+  Sizes s;
+  const size_t H = N / 2, NH = H + 1, NN = (size_t)N * N;
+  const size_t rel = o.precision == 64 ? 8 : 4, cel = 2 * rel;
+  const size_t mb = (size_t)o.max_batch;
+  const int B = auto_alpha_batch(o);
+  sigw::LaunchShape sh = o.precision == 64 ? sigw::OpsRT<double>::shape(N) : sigw::OpsRT<float>::shape(N);
+  s.maxblk = sh.maxblk_f3;
+  s.phi = mb * NN * NH * cel;
+  s.T = 2 * mb * (size_t)B * NN * H * cel;
+  s.W = mb * 3 * (size_t)o.n_alpha * NN * H * cel;
+  s.synth = mb * (NN * H * cel + NN * NH * cel + NN * (size_t)N * rel) + 1024;
+  s.F = mb * 6 * NN * NH * cel;
+  s.F2 = mb * 6 * NN * NH * cel;
+  s.partial = mb * H * 2 * (size_t)s.maxblk * sizeof(double);
+  s.out = mb * H * 4 * sizeof(double) + H * (sizeof(int) + sizeof(double));
+  const size_t msq = 3 * H * H + 1;
+  s.lut = H * msq * sizeof(int16_t);
+  s.tab = 2 * ((size_t)o.n_alpha * (o.n_modes + 1) + o.n_alpha) * rel;
+  s.tw = (size_t)N * cel;
+  s.amp = msq * rel;
+  const int rb = o.precision == 64 ? sigw::OpsRT<double>::rows_blocks(N) : sigw::OpsRT<float>::rows_blocks(N);
+  s.rows_sq = mb * ((size_t)rb * sizeof(double) + 2 * sizeof(double) + 2 * sizeof(uint64_t));
+  return s;
+}
+
+bool valid_opts(const sigw_opts& o) {
+  return o.n_modes >= 2 && o.n_modes <= 4096 && o.n_alpha >= 1 && o.n_alpha <= o.n_modes && o.umin > 0 &&
+         o.umax > o.umin && o.sigp > 0 && o.Ap >= 0 && (o.precision == 32 || o.precision == 64) &&
+         o.max_batch >= 1 && o.max_batch <= 64 && o.alpha_batch >= 0;
+}
+
+}  // namespace
+
+struct sigw_plan_s {
+  int N = 0;
+  double L = 0;
+  sigw_opts opts{};
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  sigw::Decomposition dec;
+  Sizes sz{};
+  int B = 1;
+  size_t msq_max = 0;
+  std::vector<double> Nk;  // per shell 1..N/2
+  // device buffers
+  std::vector<void*> allocs;
+  void* d_phi = nullptr;
+  void* d_T = nullptr;
+  void* d_work = nullptr;  // W during the hot loop, synthesis scratch during sigw_generate / sigw_fft3d
+  void* d_F = nullptr;
+  void* d_F2 = nullptr;
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  int* d_shells = nullptr;
+  double* d_Nk = nullptr;
+  int16_t* d_lut = nullptr;
+  void* d_phitab[2] = {nullptr, nullptr};
+  void* d_sigma[2] = {nullptr, nullptr};
+  void* d_tw = nullptr;
+  void* d_amp = nullptr;
+  double* d_sq = nullptr;
+  double* d_mean = nullptr;
+  unsigned long long* d_hits = nullptr;
+  uint64_t* d_seeds = nullptr;
+  int generated = 0;
+  std::string err;
+
+  size_t relem() const { return opts.precision == 64 ? 8 : 4; }
+  size_t celem() const { return 2 * relem(); }
+};
+
+namespace {
+
+sigw_status fail(sigw_plan p, sigw_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+sigw_status cuda_fail(sigw_plan p, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();
+  return fail(p, SIGW_ECUDA, m);
+}
+
+#define CKP(plan, call, what)                            \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(plan, _e, what); \
+  } while (0)
+
+sigw_status dev_alloc(sigw_plan p, void** ptr, size_t bytes) {
+  int c = g_fail_alloc.load();
+  if (c > 0) {
+    if (g_fail_alloc.fetch_sub(1) == 1) return fail(p, SIGW_ENOMEM, "device allocation failed (injected)");
+  }
+  cudaError_t e = cudaMalloc(ptr, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *ptr = nullptr;
+    return fail(p, e == cudaErrorMemoryAllocation ? SIGW_ENOMEM : SIGW_ECUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*ptr);
+  return SIGW_OK;
+}
+
+template <typename T>
+void to_prec(const std::vector<double>& in, std::vector<unsigned char>& out) {
+  out.resize(in.size() * sizeof(T));
+  T* o = reinterpret_cast<T*>(out.data());
+  for (size_t i = 0; i < in.size(); ++i) o[i] = (T)in[i];
+}
+
+void convert(const std::vector<double>& in, int prec, std::vector<unsigned char>& out) {
+  if (prec == 64) to_prec<double>(in, out); else to_prec<float>(in, out);
+}
+
+// modes of the full lattice n in (-N/2, N/2]^3 per shell: |n|^2 in [n_c^2 - n_c + 1, n_c^2 + n_c]
+std::vector<double> count_shell_modes(int N) {
+  const int H = N / 2;
+  const int msq_max = 3 * H * H;
+  std::vector<long long> c2(H * H + 1, 0);
+  for (int n = -H + 1; n <= H; ++n) c2[n * n] += 1;
+  std::vector<long long> hist(msq_max + 1, 0);
+  for (int a = -H + 1; a <= H; ++a)
+    for (int b = -H + 1; b <= H; ++b) {
+      const int base = a * a + b * b;
+      for (int v = 0; v <= H * H; ++v)
+        if (c2[v]) hist[base + v] += c2[v];
+    }
+  std::vector<double> nk(H + 1, 0.0);
+  for (int nc = 1; nc <= H; ++nc) {
+    long long t = 0;
+    for (int m = nc * nc - nc + 1; m <= nc * nc + nc && m <= msq_max; ++m) t += hist[m];
+    nk[nc] = (double)t;
+  }
+  return nk;
+}
+
+#define OPS(plan, fn, ...) \
+  ((plan)->opts.precision == 64 ? sigw::OpsRT<double>::fn(__VA_ARGS__) : sigw::OpsRT<float>::fn(__VA_ARGS__))
+
+}  // namespace
+
+extern "C" {
+
+sigw_status sigw_opts_default(sigw_opts* o) {
+  if (!o) return SIGW_EINVAL;
+  o->n_modes = 200;
+  o->n_alpha = 50;
+  o->umin = 1e-3;
+  o->umax = 15.0;
+  o->upiv = 1.0;
+  o->sigp = 0.5;
+  o->Ap = 10.0;
+  o->precision = 32;
+  o->alpha_batch = 0;
+  o->max_batch = 1;
+  o->strict_domain = 0;
+  return SIGW_OK;
+}
+
+const char* sigw_strerror(sigw_status s) {
+  switch (s) {
+    case SIGW_OK: return "ok";
+    case SIGW_EINVAL: return "invalid argument";
+    case SIGW_ENOMEM: return "out of memory";
+    case SIGW_ECUDA: return "CUDA error";
+    case SIGW_EDOMAIN: return "USR map argument below the floor";
+    case SIGW_ETIMEOUT: return "timed out";
+    case SIGW_EBUSY: return "request does not fit the memory budget";
+    case SIGW_ENOTREADY: return "result not ready";
+    case SIGW_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+sigw_status sigw_debug_fail_alloc(int n) {
+  g_fail_alloc.store(n > 0 ? n : 0);
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_footprint(int N, const sigw_opts* opts, size_t* bytes) {
+  sigw_opts o;
+  if (opts) o = *opts; else sigw_opts_default(&o);
+  if (!bytes || !is_pow2_in_range(N) || !valid_opts(o)) return SIGW_EINVAL;
+  *bytes = sizes_of(N, o).total();
+  return SIGW_OK;
+}
+
+sigw_status sigw_decompose(const sigw_opts* opts, int m, double* sigma, double* phi, double* edges,
+                           double* sigma_all) {
+  sigw_opts o;
+  if (opts) o = *opts; else sigw_opts_default(&o);
+  if (m < 0 || m > 1) return SIGW_EINVAL;
+  sigw::Decomposition d;
+  std::string e;
+  sigw::DecompParams p = params_of(o);
+  if (sigma_all) p.n_alpha = p.n_modes;
+  if (!sigw::build_decomposition(p, &d, &e)) return SIGW_EINVAL;
+  const sigw::KernelTerms& t = d.terms[m];
+  if (sigma) std::memcpy(sigma, t.sigma.data(), sizeof(double) * o.n_alpha);
+  if (phi) std::memcpy(phi, t.phi.data(), sizeof(double) * (size_t)o.n_alpha * o.n_modes);
+  if (edges) std::memcpy(edges, d.edges.data(), sizeof(double) * d.edges.size());
+  if (sigma_all) std::memcpy(sigma_all, t.sigma.data(), sizeof(double) * o.n_modes);
+  return SIGW_OK;
+}
+
+sigw_status sigw_cell_table(const sigw_opts* opts, int n_c, int msq_max, int16_t* lut) {
+  sigw_opts o;
+  if (opts) o = *opts; else sigw_opts_default(&o);
+  if (!lut || n_c < 1 || msq_max < 0) return SIGW_EINVAL;
+  sigw::Decomposition d;
+  std::string e;
+  if (!sigw::build_decomposition(params_of(o), &d, &e)) return SIGW_EINVAL;
+  sigw::build_cell_lut(d.edges, n_c, msq_max, lut);
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_stream, sigw_plan* out) {
+  if (!out) return SIGW_EINVAL;
+  *out = nullptr;
+  sigw_opts o;
+  if (opts) o = *opts; else sigw_opts_default(&o);
+  if (!is_pow2_in_range(N) || !(L > 0) || !valid_opts(o)) return SIGW_EINVAL;
+  sigw_plan p = new (std::nothrow) sigw_plan_s();
+  if (!p) return SIGW_ENOMEM;
+  p->N = N;
+  p->L = L;
+  p->opts = o;
+  p->B = auto_alpha_batch(o);
+  std::string e;
+  if (!sigw::build_decomposition(params_of(o), &p->dec, &e)) {
+    delete p;
+    return SIGW_EINVAL;
+  }
+  auto bail = [&](sigw_status s) {
+    sigw_plan_destroy(p);
+    return s;
+  };
+  cudaError_t ce = cudaGetDevice(&p->dev);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();
+    return bail(SIGW_ECUDA);
+  }
+  if (cuda_stream) {
+    p->st = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return bail(SIGW_ECUDA);
+    }
+    p->own_stream = true;
+  }
+  p->sz = sizes_of(N, o);
+  const int H = N / 2;
+  p->msq_max = 3 * (size_t)H * H;
+  const size_t rel = p->relem(), cel = p->celem();
+  const size_t mb = o.max_batch;
+  sigw_status s;
+#define ALLOC(ptr, bytes)                                   \
+  do {                                                      \
+    void* _q = nullptr;                                     \
+    if ((s = dev_alloc(p, &_q, (bytes))) != SIGW_OK) return bail(s); \
+    ptr = reinterpret_cast<decltype(ptr)>(_q);              \
+  } while (0)
+  ALLOC(p->d_phi, p->sz.phi);
+  ALLOC(p->d_T, p->sz.T);
+  ALLOC(p->d_work, std::max(p->sz.W, p->sz.synth));
+  ALLOC(p->d_F, p->sz.F);
+  ALLOC(p->d_F2, p->sz.F2);
+  ALLOC(p->d_partial, p->sz.partial);
+  ALLOC(p->d_out, mb * H * 4 * sizeof(double));
+  ALLOC(p->d_shells, H * sizeof(int));
+  ALLOC(p->d_Nk, H * sizeof(double));
+  ALLOC(p->d_lut, p->sz.lut);
+  for (int m = 0; m < 2; ++m) {
+    ALLOC(p->d_phitab[m], (size_t)o.n_alpha * (o.n_modes + 1) * rel);
+    ALLOC(p->d_sigma[m], (size_t)o.n_alpha * rel);
+  }
+  ALLOC(p->d_tw, (size_t)N * cel);
+  ALLOC(p->d_amp, (p->msq_max + 1) * rel);
+  const int rb = OPS(p, rows_blocks, N);
+  ALLOC(p->d_sq, mb * rb * sizeof(double));
+  ALLOC(p->d_mean, mb * sizeof(double));
+  ALLOC(p->d_hits, mb * sizeof(unsigned long long));
+  ALLOC(p->d_seeds, mb * sizeof(uint64_t));
+#undef ALLOC
+  // tables
+  std::vector<unsigned char> buf;
+  {
+    std::vector<double> tw;
+    sigw::build_twiddles(N, tw);
+    convert(tw, o.precision, buf);
+    if (cudaMemcpy(p->d_tw, buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return bail(SIGW_ECUDA);
+  }
+  for (int m = 0; m < 2; ++m) {
+    const sigw::KernelTerms& t = p->dec.terms[m];
+    std::vector<double> tab((size_t)o.n_alpha * (o.n_modes + 1), 0.0);
+    for (int a = 0; a < o.n_alpha; ++a)
+      for (int i = 0; i < o.n_modes; ++i) tab[(size_t)a * (o.n_modes + 1) + i] = t.phi[(size_t)a * o.n_modes + i];
+    convert(tab, o.precision, buf);
+    if (cudaMemcpy(p->d_phitab[m], buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return bail(SIGW_ECUDA);
+    convert(t.sigma, o.precision, buf);
+    if (cudaMemcpy(p->d_sigma[m], buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return bail(SIGW_ECUDA);
+  }
+  {
+    std::vector<int16_t> lut((size_t)H * (p->msq_max + 1));
+    for (int nc = 1; nc <= H; ++nc)
+      sigw::build_cell_lut(p->dec.edges, nc, (int)p->msq_max, lut.data() + (size_t)(nc - 1) * (p->msq_max + 1));
+    if (cudaMemcpy(p->d_lut, lut.data(), lut.size() * sizeof(int16_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(SIGW_ECUDA);
+  }
+  p->Nk = count_shell_modes(N);
+  *out = p;
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_destroy(sigw_plan p) {
+  if (!p) return SIGW_OK;
+  if (p->st) cudaStreamSynchronize(p->st);
+  for (void* q : p->allocs) cudaFree(q);
+  if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+  (void)cudaGetLastError();
+  delete p;
+  return SIGW_OK;
+}
+
+const char* sigw_plan_last_error(sigw_plan p) { return p ? p->err.c_str() : "no plan"; }
+
+sigw_status sigw_plan_kernel_terms(sigw_plan p, int m, double* sigma, double* phi, double* edges) {
+  if (!p || m < 0 || m > 1) return SIGW_EINVAL;
+  const sigw::KernelTerms& t = p->dec.terms[m];
+  if (sigma) std::memcpy(sigma, t.sigma.data(), sizeof(double) * t.sigma.size());
+  if (phi) std::memcpy(phi, t.phi.data(), sizeof(double) * t.phi.size());
+  if (edges) std::memcpy(edges, p->dec.edges.data(), sizeof(double) * p->dec.edges.size());
+  return SIGW_OK;
+}
+
+sigw_status sigw_synchronize(sigw_plan p) {
+  if (!p) return SIGW_EINVAL;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  CKP(p, cudaStreamSynchronize(p->st), "stream synchronize");
+  return SIGW_OK;
+}
+
+sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* map, const uint64_t* seeds, int batch,
+                          int64_t* usr_hits) {
+  if (!p) return SIGW_EINVAL;
+  if (!pz || !map || !seeds || batch < 1 || batch > p->opts.max_batch)
+    return fail(p, SIGW_EINVAL, "sigw_generate: bad arguments");
+  if (!(pz->A >= 0) || !(pz->sigma > 0) || !(pz->kstar > 0) || map->kind < 0 || map->kind > 2)
+    return fail(p, SIGW_EINVAL, "sigw_generate: bad P_zeta or map parameters");
+  const double floor = map->usr_floor > 0 ? map->usr_floor : 1e-6;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  const int N = p->N, H = N / 2;
+  const double L = p->L, dx = L / N, kf = 2.0 * kPi / L;
+  const size_t NN = (size_t)N * N;
+  // synthesis amplitude sqrt(P_zeta(k) dx^3) per integer |n|^2, P = 2 pi^2 Delta^2 / k^3 (Eq. eq_lognormal)
+  std::vector<double> amp(p->msq_max + 1, 0.0);
+  for (size_t msq = 1; msq <= p->msq_max; ++msq) {
+    const double k = kf * std::sqrt((double)msq);
+    const double lk = std::log(k / pz->kstar);
+    const double d2 = pz->A / std::sqrt(2.0 * kPi * pz->sigma * pz->sigma) * std::exp(-lk * lk / (2.0 * pz->sigma * pz->sigma));
+    const double P = 2.0 * kPi * kPi * d2 / (k * k * k);
+    amp[msq] = std::sqrt(P * dx * dx * dx);
+  }
+  std::vector<unsigned char> buf;
+  convert(amp, p->opts.precision, buf);
+  CKP(p, cudaMemcpyAsync(p->d_amp, buf.data(), buf.size(), cudaMemcpyHostToDevice, p->st), "upload amp");
+  CKP(p, cudaMemcpyAsync(p->d_seeds, seeds, sizeof(uint64_t) * batch, cudaMemcpyHostToDevice, p->st), "upload seeds");
+  const size_t cel = p->celem();
+  char* work = (char*)p->d_work;
+  void* Y = work;
+  void* X = work + (size_t)p->opts.max_batch * NN * H * cel;
+  void* R = (char*)X + (size_t)p->opts.max_batch * NN * (H + 1) * cel;
+  cudaStream_t st = p->st;
+  CKP(p, OPS(p, rows_r2c_noise, N, Y, p->d_seeds, batch, p->d_tw, st), "noise + rows R2C");
+  CKP(p, OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st), "forward axis 1");
+  CKP(p, OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st), "forward axis 0");
+  if (map->kind == SIGW_MAP_GAUSS) {
+    CKP(p, OPS(p, unpack, N, Y, p->d_phi, batch, p->d_amp, 2.0 / 3.0, 0, st), "unpack (Gaussian Phi)");
+  } else {
+    CKP(p, OPS(p, unpack, N, Y, X, batch, p->d_amp, 1.0, 0, st), "unpack (zeta_g)");
+    CKP(p, OPS(p, pack, N, X, Y, batch, st), "pack");
+    CKP(p, OPS(p, pass, N, Y, 0, +1, batch, p->d_tw, st), "inverse axis 0");
+    CKP(p, OPS(p, pass, N, Y, 1, +1, batch, p->d_tw, st), "inverse axis 1");
+    const double scale = 1.0 / ((double)NN * N * dx * dx * dx);
+    CKP(p, OPS(p, rows_c2r, N, Y, R, batch, scale, p->d_sq, p->d_tw, st), "rows C2R (zeta_g)");
+    const int rb = OPS(p, rows_blocks, N);
+    CKP(p, sigw::launch_reduce_mean(p->d_sq, rb, p->d_mean, batch, 1.0 / ((double)NN * N), st), "mean zeta_g^2");
+    CKP(p, cudaMemsetAsync(p->d_hits, 0, sizeof(unsigned long long) * batch, st), "memset hits");
+    sigw::MapArgs ma{map->kind, map->F_NL, map->G_NL, floor};
+    CKP(p, OPS(p, rows_r2c_map, N, R, Y, batch, ma, p->d_mean, p->d_hits, p->d_tw, st), "map + rows R2C");
+    CKP(p, OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st), "forward axis 1");
+    CKP(p, OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st), "forward axis 0");
+    CKP(p, OPS(p, unpack, N, Y, p->d_phi, batch, nullptr, (2.0 / 3.0) * dx * dx * dx, 1, st), "unpack (Phi)");
+  }
+  std::vector<unsigned long long> hits(batch, 0);
+  if (map->kind == SIGW_MAP_USR)
+    CKP(p, cudaMemcpyAsync(hits.data(), p->d_hits, sizeof(unsigned long long) * batch, cudaMemcpyDeviceToHost, st),
+        "download hits");
+  CKP(p, cudaStreamSynchronize(st), "synthesis");
+  p->generated = batch;
+  bool any = false;
+  for (int b = 0; b < batch; ++b) {
+    if (usr_hits) usr_hits[b] = (int64_t)hits[b];
+    any = any || hits[b] > 0;
+  }
+  if (any && p->opts.strict_domain) return fail(p, SIGW_EDOMAIN, "USR floor hits in strict mode");
+  return SIGW_OK;
+}
+
+sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, double* dev_out) {
+  if (!p) return SIGW_EINVAL;
+  if (!p->generated) return fail(p, SIGW_ESTATE, "sigw_spectrum before sigw_generate");
+  const int N = p->N, H = N / 2;
+  std::vector<int> sh;
+  if (shells) {
+    if (n_shells < 1 || n_shells > H) return fail(p, SIGW_EINVAL, "n_shells out of range");
+    sh.assign(shells, shells + n_shells);
+  } else {
+    for (int s = 1; s <= H; ++s) sh.push_back(s);
+  }
+  for (int s : sh)
+    if (s < 1 || s > H) return fail(p, SIGW_EINVAL, "shell index out of range");
+  const int ns = (int)sh.size();
+  const int batch = p->generated;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  std::vector<double> nk(ns);
+  for (int i = 0; i < ns; ++i) nk[i] = p->Nk[sh[i]];
+  cudaStream_t st = p->st;
+  CKP(p, cudaMemcpyAsync(p->d_shells, sh.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st), "upload shells");
+  CKP(p, cudaMemcpyAsync(p->d_Nk, nk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st), "upload Nk");
+  const int n_alpha = p->opts.n_alpha, nm1 = p->opts.n_modes + 1;
+  const size_t NN = (size_t)N * N;
+  const size_t cel = p->celem();
+  void* Ta = p->d_T;
+  void* Tb = (char*)p->d_T + (size_t)batch * p->B * NN * H * cel;
+  const long pbs = (long)ns * 2 * p->sz.maxblk;
+  for (int si = 0; si < ns; ++si) {
+    const int n_c = sh[si];
+    const int16_t* lut = p->d_lut + (size_t)(n_c - 1) * (p->msq_max + 1);
+    for (int m = 0; m < 2; ++m) {
+      for (int a0 = 0; a0 < n_alpha; a0 += p->B) {
+        const int nb = std::min(p->B, n_alpha - a0);
+        CKP(p, OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, st), "P1");
+        CKP(p, OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, st), "P2");
+      }
+      CKP(p, OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, st), "P3");
+      CKP(p, OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st), "F2");
+      CKP(p, OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st),
+          "F3");
+    }
+  }
+  const sigw::LaunchShape shp = OPS(p, shape, N);
+  CKP(p, sigw::launch_fin(p->d_partial, pbs, p->sz.maxblk, ns, p->d_shells, p->d_Nk, N, p->L, shp.tc_f3,
+                          dev_out ? dev_out : p->d_out, batch, st),
+      "bin finalise");
+  return SIGW_OK;
+}
+
+sigw_status sigw_spectrum(sigw_plan p, const int* shells, int n_shells, double* omega, double* PA, double* PB,
+                          int64_t* Nk) {
+  if (!p) return SIGW_EINVAL;
+  sigw_status s = sigw_spectrum_async(p, shells, n_shells, nullptr);
+  if (s != SIGW_OK) return s;
+  const int ns = shells ? n_shells : p->N / 2;
+  const int batch = p->generated;
+  std::vector<double> host((size_t)batch * ns * 4);
+  CKP(p, cudaMemcpyAsync(host.data(), p->d_out, host.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st),
+      "download results");
+  CKP(p, cudaStreamSynchronize(p->st), "spectrum");
+  for (int i = 0; i < batch * ns; ++i) {
+    if (PA) PA[i] = host[4 * i + 0];
+    if (PB) PB[i] = host[4 * i + 1];
+    if (Nk) Nk[i] = (int64_t)host[4 * i + 2];
+    if (omega) omega[i] = host[4 * i + 3];
+  }
+  return SIGW_OK;
+}
+
+sigw_status sigw_copy_phi(sigw_plan p, int b, void* host_out) {
+  if (!p || !host_out) return SIGW_EINVAL;
+  if (b < 0 || b >= p->generated) return fail(p, SIGW_ESTATE, "no generated field for this index");
+  const int N = p->N;
+  const size_t bytes = (size_t)N * N * (N / 2 + 1) * p->celem();
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  CKP(p, cudaMemcpyAsync(host_out, (char*)p->d_phi + (size_t)b * bytes, bytes, cudaMemcpyDeviceToHost, p->st),
+      "copy Phi");
+  CKP(p, cudaStreamSynchronize(p->st), "copy Phi");
+  return SIGW_OK;
+}
+
+sigw_status sigw_fft3d(sigw_plan p, int direction, const void* in_dev, void* out_dev) {
+  if (!p || !in_dev || !out_dev || (direction != -1 && direction != 1)) return SIGW_EINVAL;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  const int N = p->N;
+  void* Y = p->d_work;
+  cudaStream_t st = p->st;
+  if (direction < 0) {
+    CKP(p, OPS(p, rows_r2c_real, N, in_dev, Y, 1, p->d_tw, st), "rows R2C");
+    CKP(p, OPS(p, pass, N, Y, 1, -1, 1, p->d_tw, st), "forward axis 1");
+    CKP(p, OPS(p, pass, N, Y, 0, -1, 1, p->d_tw, st), "forward axis 0");
+    CKP(p, OPS(p, unpack, N, Y, out_dev, 1, nullptr, 1.0, 1, st), "unpack");
+  } else {
+    CKP(p, OPS(p, pack, N, in_dev, Y, 1, st), "pack");
+    CKP(p, OPS(p, pass, N, Y, 0, +1, 1, p->d_tw, st), "inverse axis 0");
+    CKP(p, OPS(p, pass, N, Y, 1, +1, 1, p->d_tw, st), "inverse axis 1");
+    CKP(p, OPS(p, rows_c2r, N, Y, out_dev, 1, 1.0, nullptr, p->d_tw, st), "rows C2R");
+  }
+  return SIGW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+// Device FFT building blocks: in-register radix-2/4/8/16 DFTs and a mixed-radix
+// Stockham pencil transform with shared-memory exchanges between stages.
+//
+// A length-N pencil (N = 2^p, 8 <= N <= 512) is owned by P = N/E threads, each
+// holding E complex values.  On entry thread j holds x[j + r*P] in v[r]; on exit
+// it holds X[j + r*P] in v[r].  That convention makes global loads and stores of
+// a pencil coalesced whether the pencil is contiguous (consecutive j -> consecutive
+// addresses) or one column of a tile of adjacent pencils.
+//
+// Stage s (radix R, span Ns = product of the earlier radices) is the Stockham
+// autosort step: butterfly jj reads in[jj + r N/R], multiplies by W_{Ns R}^{r (jj mod Ns)},
+// applies DFT_R and writes out[(jj/Ns) Ns R + jj mod Ns + r Ns].  All stages but the
+// last have radix E; the last has radix N / E^(S-1).  Twiddles come from a table of
+// the N-th roots of unity built on the host in FP64 (stored in the working precision).
+// DIR = -1 is the forward transform e^{-2 pi i k n / N}, DIR = +1 the unnormalised inverse.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sigw {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using cx = typename vec2<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> sub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cx<T> conjg(cx<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ cx<T> scale(cx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by i*DIR (DIR = +1: i, DIR = -1: -i)
+template <typename T, int DIR> __device__ __forceinline__ cx<T> mul_i(cx<T> a) {
+  return DIR > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+// multiply by the root W = (c + i DIR s)
+template <typename T, int DIR> __device__ __forceinline__ cx<T> rot(cx<T> a, T c, T s) {
+  return DIR > 0 ? mk<T>(a.x * c - a.y * s, a.x * s + a.y * c) : mk<T>(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+// ---------------------------------------------------------------- in-register DFTs
+template <typename T, int DIR> __device__ __forceinline__ void dft2(cx<T>& a, cx<T>& b) {
+  cx<T> t = a;
+  a = add<T>(t, b);
+  b = sub<T>(t, b);
+}
+
+template <typename T, int DIR> __device__ __forceinline__ void dft4(cx<T>* v) {
+  cx<T> s0 = add<T>(v[0], v[2]), d0 = sub<T>(v[0], v[2]);
+  cx<T> s1 = add<T>(v[1], v[3]), d1 = mul_i<T, DIR>(sub<T>(v[1], v[3]));
+  v[0] = add<T>(s0, s1);
+  v[2] = sub<T>(s0, s1);
+  v[1] = add<T>(d0, d1);
+  v[3] = sub<T>(d0, d1);
+}
+
+// radix-2 split of an 8-point DFT into two 4-point DFTs
+template <typename T, int DIR> __device__ __forceinline__ void dft8(cx<T>* v) {
+  const T h = (T)0.70710678118654752440;  // sqrt(2)/2
+  cx<T> e[4] = {v[0], v[2], v[4], v[6]};
+  cx<T> o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<T, DIR>(e);
+  dft4<T, DIR>(o);
+  o[1] = rot<T, DIR>(o[1], h, h);
+  o[2] = mul_i<T, DIR>(o[2]);
+  o[3] = rot<T, DIR>(o[3], -h, h);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = add<T>(e[k], o[k]);
+    v[k + 4] = sub<T>(e[k], o[k]);
+  }
+}
+
+template <typename T, int DIR> __device__ __forceinline__ void dft16(cx<T>* v) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin (pi/8)
+  const T h = (T)0.70710678118654752440;
+  cx<T> e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+  dft8<T, DIR>(e);
+  dft8<T, DIR>(o);
+  o[1] = rot<T, DIR>(o[1], c1, s1);
+  o[2] = rot<T, DIR>(o[2], h, h);
+  o[3] = rot<T, DIR>(o[3], s1, c1);
+  o[4] = mul_i<T, DIR>(o[4]);
+  o[5] = rot<T, DIR>(o[5], -s1, c1);
+  o[6] = rot<T, DIR>(o[6], -h, h);
+  o[7] = rot<T, DIR>(o[7], -c1, s1);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = add<T>(e[k], o[k]);
+    v[k + 8] = sub<T>(e[k], o[k]);
+  }
+}
+
+template <typename T, int DIR, int R> __device__ __forceinline__ void dftR(cx<T>* v) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<T, DIR>(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4<T, DIR>(v);
+  } else if constexpr (R == 8) {
+    dft8<T, DIR>(v);
+  } else if constexpr (R == 16) {
+    dft16<T, DIR>(v);
+  } else {
+    static_assert(R == 16, "unsupported radix");
+  }
+}
+
+// ---------------------------------------------------------------- Stockham pencil
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int N, int E> struct StockPlan {
+  static_assert((N & (N - 1)) == 0 && (E & (E - 1)) == 0, "powers of two");
+  static constexpr int P = N / E;
+  static constexpr int LE = ilog2c(E);
+  static constexpr int LN = ilog2c(N);
+  static constexpr int S = (LN + LE - 1) / LE;           // number of stages
+  static constexpr int RLAST = N / ipow(E, S - 1);       // radix of the last stage
+  static_assert(RLAST >= 2 && RLAST <= E, "bad factorisation");
+};
+
+// Shared-memory footprint of one pencil's exchange buffers: two ping-pong buffers,
+// each with separate re / im arrays of pencil_buf_elems<N>() elements of T.
+template <int N> __host__ __device__ constexpr int pencil_buf_elems() { return N + N / 32 + 1; }
+template <int N> __host__ __device__ constexpr int pencil_smem_elems() { return 4 * pencil_buf_elems<N>(); }
+__device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
+
+struct SyncBlock { __device__ __forceinline__ void operator()() const { __syncthreads(); } };
+struct SyncWarp { __device__ __forceinline__ void operator()() const { __syncwarp(); } };
+
+// tw[k] = exp(-2 pi i k / N), k = 0..N-1 (FP64-generated, stored in T)
+template <typename T, int DIR>
+__device__ __forceinline__ cx<T> twiddle(const cx<T>* __restrict__ tw, int idx) {
+  cx<T> w = __ldg(tw + idx);
+  return DIR > 0 ? conjg<T>(w) : w;
+}
+template <> __device__ __forceinline__ cx<double> twiddle<double, 1>(const cx<double>* __restrict__ tw, int idx) {
+  cx<double> w = tw[idx];
+  return conjg<double>(w);
+}
+template <> __device__ __forceinline__ cx<double> twiddle<double, -1>(const cx<double>* __restrict__ tw, int idx) {
+  return tw[idx];
+}
+
+// Stage s >= 1 of the Stockham recursion: reads buffer (s-1)&1, writes buffer s&1.
+template <typename T, int N, int E, int DIR, int s, typename Sync>
+__device__ __forceinline__ void stock_stage(cx<T> (&v)[E], int j, T* __restrict__ sm, const cx<T>* __restrict__ tw,
+                                            Sync sync) {
+  using PL = StockPlan<N, E>;
+  constexpr int P = PL::P;
+  constexpr int S = PL::S;
+  constexpr int B = pencil_buf_elems<N>();
+  constexpr int Ns = ipow(E, s);
+  const T* rre = sm + ((s - 1) & 1) * 2 * B;
+  const T* rim = rre + B;
+  if constexpr (s < S - 1) {
+    T* wre = sm + (s & 1) * 2 * B;
+    T* wim = wre + B;
+    const int jj = j;
+    const int k = jj & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int p = padx(jj + r * P);
+      v[r] = mk<T>(rre[p], rim[p]);
+    }
+    constexpr int stride = N / (Ns * E);
+#pragma unroll
+    for (int r = 1; r < E; ++r) v[r] = mul<T>(v[r], twiddle<T, DIR>(tw, r * k * stride));
+    dftR<T, DIR, E>(v);
+    const int base = (jj / Ns) * Ns * E + k;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int p = padx(base + r * Ns);
+      wre[p] = v[r].x;
+      wim[p] = v[r].y;
+    }
+    sync();
+    stock_stage<T, N, E, DIR, s + 1, Sync>(v, j, sm, tw, sync);
+  } else {
+    constexpr int R = PL::RLAST;
+    constexpr int NB = E / R;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int jj = j + t * P;
+      const int k = jj & (Ns - 1);
+      cx<T> a[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int p = padx(jj + r * (N / R));
+        a[r] = mk<T>(rre[p], rim[p]);
+      }
+      constexpr int stride = N / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) a[r] = mul<T>(a[r], twiddle<T, DIR>(tw, r * k * stride));
+      dftR<T, DIR, R>(a);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[t + r * NB] = a[r];
+    }
+  }
+}
+
+// Full pencil transform (see the file header for the data convention).  `sm` points to this
+// pencil's pencil_smem_elems<N>() elements.  Every thread of the synchronisation group must call
+// it (no divergent early exit).  With TRAIL, a final barrier lets the caller reuse `sm` at once.
+template <typename T, int N, int E, int DIR, typename Sync, bool TRAIL = true>
+__device__ __forceinline__ void fft_pencil(cx<T> (&v)[E], int j, T* __restrict__ sm, const cx<T>* __restrict__ tw,
+                                           Sync sync) {
+  using PL = StockPlan<N, E>;
+  if constexpr (PL::S == 1) {
+    dftR<T, DIR, E>(v);
+  } else {
+    constexpr int B = pencil_buf_elems<N>();
+    T* wre = sm;
+    T* wim = sm + B;
+    dftR<T, DIR, E>(v);
+    const int base = j * E;  // Ns = 1
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int p = padx(base + r);
+      wre[p] = v[r].x;
+      wim[p] = v[r].y;
+    }
+    sync();
+    stock_stage<T, N, E, DIR, 1, Sync>(v, j, sm, tw, sync);
+    if constexpr (TRAIL) sync();
+  }
+}
+
+}  // namespace sigw

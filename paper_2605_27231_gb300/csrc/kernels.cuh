@@ -1,0 +1,742 @@
+// Device kernels of the lattice SIGW path, templated on the working precision T
+// (float or double) and the lattice size N.  Included by one translation unit per
+// precision, which instantiates them and defines the sigw::Ops launchers.
+//
+// Layouts (b = realisation in the batch, H = N/2, NH = N/2 + 1):
+//   real       R[b][a0][a1][a2]                      N^3 values
+//   standard   X[b][k0][k1][k2], k2 = 0..H           the usual half spectrum (Phi~ is kept this way)
+//   packed     Y[b][a0|k0][a1|k1][c], c = 0..H-1     column 0 holds (k2 = 0) + i (k2 = H); this is
+//              exact because both planes are transforms of real 2-D fields, and it makes every
+//              strided pass run over exactly H columns.
+// Lattice wave numbers: index k -> n = k for k <= H, k - N otherwise (index H is +N/2).
+// The derivative factor uses n^D = 0 on the Nyquist index H.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+#include "ops.h"
+
+namespace sigw {
+
+__device__ __forceinline__ int wrapn(int k, int N) { return k <= (N >> 1) ? k : k - N; }
+__device__ __forceinline__ int derivn(int k, int N) { return k == (N >> 1) ? 0 : wrapn(k, N); }
+
+// ---------------------------------------------------------------- Philox4x32-10 (SC'11)
+// counter (c0, c1, c2, c3), key (k0, k1); 10 rounds, Weyl key schedule between rounds.
+__device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
+                                         uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+}
+
+// N(0,1) draw for lattice cell `cell` (row-major linear index) and key `seed`: Box-Muller in FP64 on
+// two 53-bit uniforms made from the four output words, u1 in (0, 1], u2 in [0, 1).
+__device__ __forceinline__ double gauss_draw(uint32_t cell, uint64_t seed) {
+  uint32_t c0 = cell, c1 = 0u, c2 = 0u, c3 = 0u;
+  philox10(c0, c1, c2, c3, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+  const uint64_t a = ((((uint64_t)c0) << 32) | c1) >> 11;
+  const uint64_t bb = ((((uint64_t)c2) << 32) | c3) >> 11;
+  const double u1 = ((double)a + 1.0) * 1.1102230246251565404e-16;  // 2^-53
+  const double u2 = (double)bb * 1.1102230246251565404e-16;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// ---------------------------------------------------------------- shapes
+template <typename T, int N> struct Shape {
+  static constexpr int H = N / 2;
+  // strided passes: E values per thread, TC columns per CTA
+  static constexpr int ES = (sizeof(T) == 4) ? (N >= 256 ? 16 : (N >= 16 ? 8 : 4)) : (N >= 16 ? 8 : 4);
+  static constexpr int PS = N / ES;
+  static constexpr int TC0 = 256 / PS;
+  static constexpr int TC = TC0 < 1 ? 1 : (TC0 > H ? H : TC0);
+  // row passes: E values per thread, RPC rows per CTA
+  static constexpr int ER = (N >= 16) ? 8 : 4;
+  static constexpr int PR = N / ER;
+  static constexpr int RPC0 = 256 / PR;
+  static constexpr int RPC = RPC0 > (N * N / 2) ? (N * N / 2) : RPC0;
+  // forward-a0 + TT pass keeps six spectra per thread: fewer values per thread
+  static constexpr int E3 = (sizeof(T) == 4) ? (N >= 16 ? 8 : 4) : 4;
+  static constexpr int P3 = N / E3;
+  static constexpr int TC3_0 = 256 / P3;
+  static constexpr int TC3_1 = TC3_0 < 1 ? 1 : (TC3_0 > 8 ? 8 : TC3_0);
+  static constexpr int TC3 = TC3_1 * P3 < 32 ? 32 / P3 : TC3_1;  // whole warps (the partial sum uses shuffles)
+};
+
+template <int P> struct RowSync { using type = SyncWarp; };
+template <> struct RowSync<64> { using type = SyncBlock; };
+template <> struct RowSync<128> { using type = SyncBlock; };
+
+// ================================================================ synthesis chain
+// Two real rows (2q, 2q+1) share one complex FFT: z = x1 + i x2, Z = DFT z,
+// X1(k) = (Z(k) + Z*(N-k))/2, X2(k) = -i/2 (Z(k) - Z*(N-k)).
+// MODE 0: rows from R;  MODE 1: Philox noise;  MODE 2: R through the NG map.
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>* __restrict__ Y,
+                                                  const cx<T>* __restrict__ tw, const uint64_t* __restrict__ seeds,
+                                                  MapArgs map, const double* __restrict__ mean,
+                                                  unsigned long long* __restrict__ hits) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ER, P = SH::PR, H = N / 2;
+  constexpr int PPC = SH::RPC;  // row pairs per CTA
+  constexpr int B = pencil_buf_elems<N>();
+  using Sync = typename RowSync<P>::type;
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw) + (threadIdx.x / P) * pencil_smem_elems<N>();
+  const int j = threadIdx.x % P;
+  const int b = blockIdx.y;
+  const long pair = (long)blockIdx.x * PPC + threadIdx.x / P;
+  const bool live = pair < (long)N * N / 2;
+  const long row0 = 2 * pair;
+  cx<T> v[E];
+  unsigned long long myhits = 0;
+  double mu = 0.0;
+  if (MODE == 2) mu = mean[b];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int x = j + r * P;
+    T x1 = 0, x2 = 0;
+    if (live) {
+      if (MODE == 1) {
+        const uint64_t sd = seeds[b];
+        x1 = (T)gauss_draw((uint32_t)(row0 * N + x), sd);
+        x2 = (T)gauss_draw((uint32_t)((row0 + 1) * N + x), sd);
+      } else {
+        const T* rb = R + ((long)b * N * N + row0) * N;
+        x1 = rb[x];
+        x2 = rb[N + x];
+        if (MODE == 2) {
+          T z[2] = {x1, x2};
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const T g = z[q];
+            if (map.kind == 1) {
+              z[q] = g + (T)map.F * (g * g - (T)mu) + (T)map.G * g * g * g;
+            } else if (map.kind == 2) {
+              T arg = (T)1 - (T)3 * g;
+              if (arg < (T)map.floor) {
+                ++myhits;
+                arg = (T)map.floor;
+              }
+              z[q] = -log(arg) / (T)3;
+            }
+          }
+          x1 = z[0];
+          x2 = z[1];
+        }
+      }
+    }
+    v[r] = mk<T>(x1, x2);
+  }
+  if (MODE == 2 && map.kind == 2) {
+    // warp-reduce the hit count, one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) myhits += __shfl_down_sync(0xffffffffu, myhits, o);
+    if ((threadIdx.x & 31) == 0 && myhits) atomicAdd(hits + b, myhits);
+  }
+  fft_pencil<T, N, E, -1, Sync>(v, j, sm, tw, Sync());
+  T* zre = sm;
+  T* zim = sm + B;
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int p = padx(j + r * P);
+    zre[p] = v[r].x;
+    zim[p] = v[r].y;
+  }
+  Sync()();
+  if (live) {
+    cx<T>* y1 = Y + ((long)b * N * N + row0) * H;
+    cx<T>* y2 = y1 + H;
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) {
+      const int c = j + r * P;
+      if (c == 0) {
+        const cx<T> z0 = mk<T>(zre[0], zim[0]);
+        const int ph = padx(H);
+        const cx<T> zh = mk<T>(zre[ph], zim[ph]);
+        y1[0] = mk<T>(z0.x, zh.x);
+        y2[0] = mk<T>(z0.y, zh.y);
+      } else {
+        const int pc = padx(c), pm = padx(N - c);
+        const cx<T> zc = mk<T>(zre[pc], zim[pc]);
+        const cx<T> zm = mk<T>(zre[pm], -zim[pm]);  // conj Z(N-c)
+        y1[c] = mk<T>((T)0.5 * (zc.x + zm.x), (T)0.5 * (zc.y + zm.y));
+        y2[c] = mk<T>((T)0.5 * (zc.y - zm.y), (T)-0.5 * (zc.x - zm.x));
+      }
+    }
+  }
+}
+
+// Packed half rows -> real rows (two rows per complex inverse FFT), scaled by `scale`.
+// With SQ, per-CTA FP64 partial sums of the squared outputs go to sq_partial[b][blockIdx.x].
+template <typename T, int N, bool SQ>
+__global__ void __launch_bounds__(256) k_rows_c2r(const cx<T>* __restrict__ Y, T* __restrict__ R, T scale,
+                                                  double* __restrict__ sq_partial, const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ER, P = SH::PR, H = N / 2;
+  constexpr int PPC = SH::RPC;
+  using Sync = typename RowSync<P>::type;
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw) + (threadIdx.x / P) * pencil_smem_elems<N>();
+  __shared__ double red[32];
+  const int j = threadIdx.x % P;
+  const int b = blockIdx.y;
+  const long pair = (long)blockIdx.x * PPC + threadIdx.x / P;
+  const bool live = pair < (long)N * N / 2;
+  const long row0 = 2 * pair;
+  const cx<T>* y1 = Y + ((long)b * N * N + row0) * H;
+  const cx<T>* y2 = y1 + H;
+  cx<T> v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int k = j + r * P;
+    cx<T> a = mk<T>(0, 0), c = mk<T>(0, 0);
+    if (live) {
+      if (k == 0) {
+        a = mk<T>(y1[0].x, 0);
+        c = mk<T>(y2[0].x, 0);
+      } else if (k == H) {
+        a = mk<T>(y1[0].y, 0);
+        c = mk<T>(y2[0].y, 0);
+      } else if (k < H) {
+        a = y1[k];
+        c = y2[k];
+      } else {
+        a = conjg<T>(y1[N - k]);
+        c = conjg<T>(y2[N - k]);
+      }
+    }
+    v[r] = mk<T>(a.x - c.y, a.y + c.x);  // a + i c
+  }
+  fft_pencil<T, N, E, +1, Sync>(v, j, sm, tw, Sync());
+  double sq = 0.0;
+  if (live) {
+    T* r1 = R + ((long)b * N * N + row0) * N;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int x = j + r * P;
+      const T u = v[r].x * scale, w = v[r].y * scale;
+      r1[x] = u;
+      r1[N + x] = w;
+      if (SQ) sq += (double)u * (double)u + (double)w * (double)w;
+    }
+  }
+  if (SQ) {
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+      sq_partial[(long)b * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// In-place C2C transforms along axis 0 (AX = 0, stride N*H) or axis 1 (AX = 1, stride H) of a packed array.
+template <typename T, int N, int DIR, int AX>
+__global__ void __launch_bounds__(256) k_pass(cx<T>* __restrict__ Y, const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
+  extern __shared__ unsigned char smraw[];
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const int col = blockIdx.x * TC + c;
+  const int o = blockIdx.y;
+  const int b = blockIdx.z;
+  const long stride = AX == 0 ? (long)N * H : (long)H;
+  const long ostride = AX == 0 ? (long)H : (long)N * H;
+  cx<T>* base = Y + (long)b * N * N * H + o * ostride + col;
+  cx<T> v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) v[r] = base[(j + r * P) * stride];
+  fft_pencil<T, N, E, DIR, SyncBlock, false>(v, j, sm, tw, SyncBlock());
+#pragma unroll
+  for (int r = 0; r < E; ++r) base[(j + r * P) * stride] = v[r];
+}
+
+// Packed -> standard.  MODE 0 (synthesis): times amp[|n|^2] * factor, zero on k = 0 and the Nyquist planes.
+// MODE 1: times factor.
+template <typename T, int MODE>
+__global__ void k_unpack(const cx<T>* __restrict__ Y, cx<T>* __restrict__ X, int N, const T* __restrict__ amp,
+                         T factor, long total) {
+  const int H = N / 2, NH = H + 1;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int k2 = (int)(i % NH);
+    const long q = i / NH;
+    const int k1 = (int)(q % N);
+    const long q2 = q / N;
+    const int k0 = (int)(q2 % N);
+    const long b = q2 / N;
+    cx<T> val;
+    if (k2 >= 1 && k2 < H) {
+      val = Y[((b * N + k0) * N + k1) * H + k2];
+    } else {
+      const cx<T> yk = Y[((b * N + k0) * N + k1) * H];
+      const cx<T> ym = Y[((b * N + ((N - k0) & (N - 1))) * N + ((N - k1) & (N - 1))) * H];
+      if (k2 == 0)
+        val = mk<T>((T)0.5 * (yk.x + ym.x), (T)0.5 * (yk.y - ym.y));
+      else
+        val = mk<T>((T)0.5 * (yk.y + ym.y), (T)-0.5 * (yk.x - ym.x));
+    }
+    if (MODE == 0) {
+      const int n0 = wrapn(k0, N), n1 = wrapn(k1, N);
+      const int msq = n0 * n0 + n1 * n1 + k2 * k2;
+      const bool zero = (k0 == H) || (k1 == H) || (k2 == H) || msq == 0;
+      const T a = zero ? (T)0 : amp[msq] * factor;
+      val = mk<T>(val.x * a, val.y * a);
+    } else {
+      val = mk<T>(val.x * factor, val.y * factor);
+    }
+    X[i] = val;
+  }
+}
+
+template <typename T>
+__global__ void k_pack(const cx<T>* __restrict__ X, cx<T>* __restrict__ Y, int N, long total) {
+  const int H = N / 2, NH = H + 1;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % H);
+    const long q = i / H;
+    const cx<T>* xr = X + q * NH;
+    if (c == 0) {
+      const cx<T> x0 = xr[0], xh = xr[H];
+      Y[i] = mk<T>(x0.x - xh.y, x0.y + xh.x);  // X(0) + i X(H)
+    } else {
+      Y[i] = xr[c];
+    }
+  }
+}
+
+#ifdef SIGW_COMMON_KERNELS
+__global__ void k_reduce_mean(const double* __restrict__ part, int nblk, double* __restrict__ mean, double inv) {
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nblk; ++i) t += part[(long)b * nblk + i];
+    mean[b] = t * inv;
+  }
+}
+#endif
+
+// ================================================================ hot path
+// P1: first inverse pass along axis 0 for a tile of TC packed columns at fixed k1.
+//   V_a(n) = phi_a(cell(|n|^2)) Phi~(n)          (column 0: V(k2=0) + i V(k2=H), each with its own cell)
+//   Ta_a = IDFT_0[V_a],  Tb_a = IDFT_0[i n0^D V_a]
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>* __restrict__ Ta,
+                                            cx<T>* __restrict__ Tb, const int16_t* __restrict__ lut,
+                                            const T* __restrict__ phitab, int nm1, int alpha0, int nb,
+                                            const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2, NH = H + 1;
+  extern __shared__ unsigned char smraw[];
+  T* sm_pen = reinterpret_cast<T*>(smraw);
+  T* sm_tab = sm_pen + TC * pencil_smem_elems<N>();   // nb * nm1
+  cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(sm_tab + ((nb * nm1 + 1) & ~1));  // N values (column 0 only)
+  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);                              // N cells
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  T* sm = sm_pen + c * pencil_smem_elems<N>();
+  const int cc = blockIdx.x * TC + c;
+  const int k1 = blockIdx.y;
+  const int b = blockIdx.z;
+  const int n1 = wrapn(k1, N);
+  for (int i = threadIdx.x; i < nb * nm1; i += blockDim.x) sm_tab[i] = phitab[(long)alpha0 * nm1 + i];
+  const cx<T>* pb = phi + ((long)b * N * N + k1) * NH;  // + k0 * N * NH + k2
+  if (blockIdx.x == 0) {
+    for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
+      const int n0 = wrapn(k0, N);
+      sm_nyq[k0] = pb[(long)k0 * N * NH + H];
+      sm_cn[k0] = lut[n0 * n0 + n1 * n1 + H * H];
+    }
+  }
+  cx<T> ph[E];
+  int cell[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int k0 = j + r * P;
+    const int n0 = wrapn(k0, N);
+    ph[r] = pb[(long)k0 * N * NH + cc];
+    cell[r] = lut[n0 * n0 + n1 * n1 + cc * cc];
+  }
+  __syncthreads();
+  const long fstride = (long)N * N * H;  // one field
+  for (int a = 0; a < nb; ++a) {
+    const T* tab = sm_tab + a * nm1;
+    cx<T> v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const T f = tab[cell[r]];
+      v[r] = mk<T>(f * ph[r].x, f * ph[r].y);
+      if (cc == 0) {
+        const int k0 = j + r * P;
+        const T fn = tab[sm_cn[k0]];
+        const cx<T> yn = sm_nyq[k0];
+        v[r] = mk<T>(v[r].x - fn * yn.y, v[r].y + fn * yn.x);
+      }
+    }
+    cx<T> w[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const T nd = (T)derivn(j + r * P, N);
+      w[r] = mk<T>(-nd * v[r].y, nd * v[r].x);  // i n0 v
+    }
+    fft_pencil<T, N, E, +1, SyncBlock>(v, j, sm, tw, SyncBlock());
+    cx<T>* ta = Ta + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
+#pragma unroll
+    for (int r = 0; r < E; ++r) ta[(long)(j + r * P) * N * H] = v[r];
+    fft_pencil<T, N, E, +1, SyncBlock>(w, j, sm, tw, SyncBlock());
+    cx<T>* tb = Tb + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
+#pragma unroll
+    for (int r = 0; r < E; ++r) tb[(long)(j + r * P) * N * H] = w[r];
+  }
+}
+
+// P2: second inverse pass along axis 1 at fixed a0.  For term a:
+//   W[0] = IDFT_1[Ta]            (G_2 after i n2 and the last pass)
+//   W[1] = IDFT_1[i n1^D Ta]     (G_1)
+//   W[2] = IDFT_1[Tb]            (G_0)
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
+                                            cx<T>* __restrict__ W, int n_alpha, int alpha0, int nb,
+                                            const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
+  extern __shared__ unsigned char smraw[];
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const int cc = blockIdx.x * TC + c;
+  const int a0 = blockIdx.y;
+  const int b = blockIdx.z / nb, a = blockIdx.z % nb;
+  const long fstride = (long)N * N * H;
+  const long off = (long)a0 * N * H + cc;
+  const cx<T>* ta = Ta + ((long)b * nb + a) * fstride + off;
+  const cx<T>* tb = Tb + ((long)b * nb + a) * fstride + off;
+  cx<T> v[E], w[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    v[r] = ta[(long)(j + r * P) * H];
+    const T nd = (T)derivn(j + r * P, N);
+    w[r] = mk<T>(-nd * v[r].y, nd * v[r].x);
+  }
+  auto wout = [&](int f) { return W + (((long)b * 3 + f) * n_alpha + alpha0 + a) * fstride + off; };
+  fft_pencil<T, N, E, +1, SyncBlock>(v, j, sm, tw, SyncBlock());
+  cx<T>* o0 = wout(0);
+#pragma unroll
+  for (int r = 0; r < E; ++r) o0[(long)(j + r * P) * H] = v[r];
+  fft_pencil<T, N, E, +1, SyncBlock>(w, j, sm, tw, SyncBlock());
+  cx<T>* o1 = wout(1);
+#pragma unroll
+  for (int r = 0; r < E; ++r) o1[(long)(j + r * P) * H] = w[r];
+#pragma unroll
+  for (int r = 0; r < E; ++r) v[r] = tb[(long)(j + r * P) * H];
+  fft_pencil<T, N, E, +1, SyncBlock, false>(v, j, sm, tw, SyncBlock());
+  cx<T>* o2 = wout(2);
+#pragma unroll
+  for (int r = 0; r < E; ++r) o2[(long)(j + r * P) * H] = v[r];
+}
+
+// 1-D Hermitian spectrum value at index k (0..N-1) of a packed row:
+//   plain: k = 0 -> Re row[0], k = H -> Im row[0], else row[k] or conj(row[N-k]);
+//   grad : i n^D(k) times the plain value, zero at k = 0 and k = H (the packed column is not read).
+template <typename T, int N>
+__device__ __forceinline__ cx<T> herm_plain(const cx<T>* __restrict__ row, int k) {
+  constexpr int H = N / 2;
+  if (k == 0) return mk<T>(__ldg(&row[0].x), (T)0);
+  if (k == H) return mk<T>(__ldg(&row[0].y), (T)0);
+  if (k < H) return __ldg(row + k);
+  return conjg<T>(__ldg(row + (N - k)));
+}
+template <typename T, int N>
+__device__ __forceinline__ cx<T> herm_grad(const cx<T>* __restrict__ row, int k) {
+  constexpr int H = N / 2;
+  if (k == 0 || k == H) return mk<T>((T)0, (T)0);
+  cx<T> x;
+  T n;
+  if (k < H) {
+    x = __ldg(row + k);
+    n = (T)k;
+  } else {
+    x = conjg<T>(__ldg(row + (N - k)));
+    n = (T)(k - N);
+  }
+  return mk<T>(-n * x.y, n * x.x);
+}
+
+// P3: last inverse pass (axis 2, C2R) of all terms for RPC rows, the product
+//   s_ij(x) = sum_a sigma_a g^a_i(x) g^a_j(x)  (six components, FP32/FP64 registers),
+// then the forward R2C of s_ij along axis 2 keeping k2 = 0..n_c, written to F[b][comp][a0][a1][k2].
+// Term pair (a, a+1) uses three complex transforms: (g2^a + i g1^a), (g0^a + i g0^{a+1}), (g2^{a+1} + i g1^{a+1}).
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_p3(const cx<T>* __restrict__ W, const T* __restrict__ sigma, int n_alpha,
+                                            cx<T>* __restrict__ F, int n_c, const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ER, P = SH::PR, H = N / 2, RPC = SH::RPC;
+  constexpr int B = pencil_buf_elems<N>();
+  using Sync = typename RowSync<P>::type;
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw) + (threadIdx.x / P) * pencil_smem_elems<N>();
+  const int j = threadIdx.x % P;
+  const long row = (long)blockIdx.x * RPC + threadIdx.x / P;  // a0 * N + a1 (always < N*N: RPC divides N*N)
+  const int b = blockIdx.y;
+  const long fstride = (long)N * N * H;
+  auto wrow = [&](int f, int a) { return W + (((long)b * 3 + f) * n_alpha + a) * fstride + row * H; };
+  T acc[6][E];
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+#pragma unroll
+    for (int r = 0; r < E; ++r) acc[q][r] = (T)0;
+  for (int a = 0; a < n_alpha; a += 2) {
+    const bool two = (a + 1) < n_alpha;
+    const cx<T>* wb0 = wrow(0, a);
+    const cx<T>* w10 = wrow(1, a);
+    const cx<T>* w20 = wrow(2, a);
+    const cx<T>* wb1 = wrow(0, two ? a + 1 : a);
+    const cx<T>* w11 = wrow(1, two ? a + 1 : a);
+    const cx<T>* w21 = wrow(2, two ? a + 1 : a);
+    cx<T> zA[E], zB[E], zC[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int k = j + r * P;
+      const cx<T> g2 = herm_grad<T, N>(wb0, k), g1 = herm_plain<T, N>(w10, k);
+      const cx<T> g0 = herm_plain<T, N>(w20, k);
+      cx<T> g0b = herm_plain<T, N>(w21, k);
+      if (!two) g0b = mk<T>((T)0, (T)0);
+      const cx<T> h2 = herm_grad<T, N>(wb1, k), h1 = herm_plain<T, N>(w11, k);
+      zA[r] = mk<T>(g2.x - g1.y, g2.y + g1.x);
+      zB[r] = mk<T>(g0.x - g0b.y, g0.y + g0b.x);
+      zC[r] = mk<T>(h2.x - h1.y, h2.y + h1.x);
+    }
+    fft_pencil<T, N, E, +1, Sync>(zA, j, sm, tw, Sync());
+    fft_pencil<T, N, E, +1, Sync>(zB, j, sm, tw, Sync());
+    fft_pencil<T, N, E, +1, Sync>(zC, j, sm, tw, Sync());
+    const T sa = sigma[a];
+    const T sb = two ? sigma[a + 1] : (T)0;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      {
+        const T g0 = zB[r].x, g1 = zA[r].y, g2 = zA[r].x;
+        const T s0 = sa * g0, s1 = sa * g1;
+        acc[0][r] += s0 * g0;
+        acc[1][r] += s1 * g1;
+        acc[2][r] += sa * g2 * g2;
+        acc[3][r] += s0 * g1;
+        acc[4][r] += s0 * g2;
+        acc[5][r] += s1 * g2;
+      }
+      {
+        const T g0 = zB[r].y, g1 = zC[r].y, g2 = zC[r].x;
+        const T s0 = sb * g0, s1 = sb * g1;
+        acc[0][r] += s0 * g0;
+        acc[1][r] += s1 * g1;
+        acc[2][r] += sb * g2 * g2;
+        acc[3][r] += s0 * g1;
+        acc[4][r] += s0 * g2;
+        acc[5][r] += s1 * g2;
+      }
+    }
+  }
+  // forward R2C of the six real rows, two per complex transform
+  T* zre = sm;
+  T* zim = sm + B;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    cx<T> z[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) z[r] = mk<T>(acc[2 * q][r], acc[2 * q + 1][r]);
+    fft_pencil<T, N, E, -1, Sync>(z, j, sm, tw, Sync());
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int p = padx(j + r * P);
+      zre[p] = z[r].x;
+      zim[p] = z[r].y;
+    }
+    Sync()();
+    const int ncp = n_c + 1;
+    cx<T>* f1 = F + (((long)b * 6 + 2 * q) * N * N + row) * ncp;
+    cx<T>* f2 = F + (((long)b * 6 + 2 * q + 1) * N * N + row) * ncp;
+    for (int k = j; k <= n_c; k += P) {
+      const int pk = padx(k), pm = padx((N - k) & (N - 1));
+      const T zr = zre[pk], zi = zim[pk], mr = zre[pm], mi = -zim[pm];
+      f1[k] = mk<T>((T)0.5 * (zr + mr), (T)0.5 * (zi + mi));
+      f2[k] = mk<T>((T)0.5 * (zi - mi), (T)-0.5 * (zr - mr));
+    }
+    Sync()();
+  }
+}
+
+// F2: forward DFT along axis 1 of F[b][comp][a0][a1][k2] (k2 = 0..n_c), keeping n1 in [n1lo, n1lo + nk1).
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_f2(const cx<T>* __restrict__ F, cx<T>* __restrict__ F2, int n_c, int n1lo,
+                                            int nk1, const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::ES, P = SH::PS, TC = SH::TC;
+  extern __shared__ unsigned char smraw[];
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const int ncp = n_c + 1;
+  const int cc = blockIdx.x * TC + c;
+  const bool valid = cc < ncp;
+  const int a0 = blockIdx.y;
+  const long bc = blockIdx.z;  // b * 6 + comp
+  const cx<T>* in = F + (bc * N + a0) * (long)N * ncp + cc;
+  cx<T> v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) v[r] = valid ? in[(long)(j + r * P) * ncp] : mk<T>((T)0, (T)0);
+  fft_pencil<T, N, E, -1, SyncBlock, false>(v, j, sm, tw, SyncBlock());
+  if (valid) {
+    cx<T>* out = F2 + (bc * N + a0) * (long)nk1 * ncp + cc;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int idx = wrapn(j + r * P, N) - n1lo;
+      if (idx >= 0 && idx < nk1) out[(long)idx * ncp] = v[r];
+    }
+  }
+}
+
+// sum over the two polarisations of |e^l_ij(k_hat) S_ij|^2 (Sec. sec_sigw basis: u = k x e0 / |k x e0|,
+// e1 in place of e0 when k is parallel to e0, v = k x u).  S = (00, 11, 22, 01, 02, 12).
+__device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2* S) {
+  const double nn = sqrt((double)(n0 * n0 + n1 * n1 + n2 * n2));
+  const double k0 = n0 / nn, k1 = n1 / nn, k2 = n2 / nn;
+  double u0 = 0.0, u1 = k2, u2 = -k1;  // k x e0
+  double un = sqrt(u1 * u1 + u2 * u2);
+  if (un < 1e-12) {  // k x e1
+    u0 = -k2;
+    u1 = 0.0;
+    u2 = k0;
+    un = sqrt(u0 * u0 + u2 * u2);
+  }
+  u0 /= un;
+  u1 /= un;
+  u2 /= un;
+  const double v0 = k1 * u2 - k2 * u1, v1 = k2 * u0 - k0 * u2, v2 = k0 * u1 - k1 * u0;
+  // S u and S v
+  const double2 s00 = S[0], s11 = S[1], s22 = S[2], s01 = S[3], s02 = S[4], s12 = S[5];
+  auto sdot = [&](double a0, double a1, double a2, double c0, double c1, double c2) {
+    // a . S . c
+    double re = a0 * (s00.x * c0 + s01.x * c1 + s02.x * c2) + a1 * (s01.x * c0 + s11.x * c1 + s12.x * c2) +
+                a2 * (s02.x * c0 + s12.x * c1 + s22.x * c2);
+    double im = a0 * (s00.y * c0 + s01.y * c1 + s02.y * c2) + a1 * (s01.y * c0 + s11.y * c1 + s12.y * c2) +
+                a2 * (s02.y * c0 + s12.y * c1 + s22.y * c2);
+    return make_double2(re, im);
+  };
+  const double2 uu = sdot(u0, u1, u2, u0, u1, u2), vv = sdot(v0, v1, v2, v0, v1, v2), uv = sdot(u0, u1, u2, v0, v1, v2);
+  const double pr = (uu.x - vv.x) * 0.70710678118654752440, pi = (uu.y - vv.y) * 0.70710678118654752440;
+  const double xr = uv.x * 1.41421356237309504880, xi = uv.y * 1.41421356237309504880;
+  return pr * pr + pi * pi + xr * xr + xi * xi;
+}
+
+// F3: forward DFT along axis 0 of the six components for a tile of columns (n1 fixed, n2 = k2),
+// TT projection on the modes of shell n_c and the FP64 sum, one partial per CTA.
+// Half-spectrum weight: a stored mode with 0 < k2 < H also stands for its partner wrap(-n), whose
+// direction is -n_hat except on Nyquist indices; the partner is projected with its own direction.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_c, int n1lo, int nk1,
+                                            double* __restrict__ partial, long pbstride,
+                                            const cx<T>* __restrict__ tw) {
+  using SH = Shape<T, N>;
+  constexpr int E = SH::E3, P = SH::P3, TC = SH::TC3, H = N / 2;
+  extern __shared__ unsigned char smraw[];
+  __shared__ double red[32];
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const int ncp = n_c + 1;
+  const int k1i = blockIdx.y;
+  const int n1 = n1lo + k1i;
+  const int b = blockIdx.z;
+  const long blk = (long)blockIdx.y * gridDim.x + blockIdx.x;
+  const int cc0 = blockIdx.x * TC;
+  const int rmax = n_c * n_c + n_c;  // |n|^2 < (n_c + 1/2)^2
+  const int rmin = n_c * n_c - n_c + 1;  // |n|^2 >= (n_c - 1/2)^2
+  if (!(cc0 < ncp && n1 * n1 + cc0 * cc0 <= rmax)) {  // no column of this tile reaches the shell
+    if (threadIdx.x == 0) partial[(long)b * pbstride + blk] = 0.0;
+    return;
+  }
+  const int cc = cc0 + c;
+  const bool valid = cc < ncp && n1 * n1 + cc * cc <= rmax;
+  cx<T> X[6][E];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const cx<T>* in = F2 + (((long)b * 6 + q) * N * nk1 + k1i) * (long)ncp + (valid ? cc : 0);
+#pragma unroll
+    for (int r = 0; r < E; ++r) X[q][r] = valid ? in[(long)(j + r * P) * nk1 * ncp] : mk<T>((T)0, (T)0);
+    fft_pencil<T, N, E, -1, SyncBlock>(X[q], j, sm, tw, SyncBlock());
+  }
+  double acc = 0.0;
+  if (valid) {
+    const int n2 = cc;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int n0 = wrapn(j + r * P, N);
+      const int msq = n0 * n0 + n1 * n1 + n2 * n2;
+      if (msq >= rmin && msq <= rmax) {
+        double2 S[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) S[q] = make_double2((double)X[q][r].x, (double)X[q][r].y);
+        acc += tt_power(n0, n1, n2, S);
+        if (n2 > 0 && n2 < H) {
+          const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
+          acc += tt_power(p0, p1, -n2, S);
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    partial[(long)b * pbstride + blk] = t;
+  }
+}
+
+#ifdef SIGW_COMMON_KERNELS
+// Deterministic second-stage reduction and the Omega constants:
+//   P_X = C^2 sum / (V N_k), C = 4 dx^3 / (n_c^2 V^2), Omega = k_c^3 / (48 pi^2) (P_A + P_B).
+__global__ void k_fin(const double* __restrict__ partial, long pbstride, int maxblk, int n_shells,
+                      const int* __restrict__ shells, const double* __restrict__ Nk, int N, double L, int tc3,
+                      double* __restrict__ out, int batch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch * n_shells) return;
+  const int b = i / n_shells, s = i % n_shells;
+  const int n_c = shells[s];
+  const int H = N / 2;
+  const int n1lo = max(-n_c, -H + 1), n1hi = min(n_c, H);
+  const int nk1 = n1hi - n1lo + 1;
+  const int nblk = ((n_c + 1 + tc3 - 1) / tc3) * nk1;
+  double sum[2];
+  for (int m = 0; m < 2; ++m) {
+    const double* p = partial + (long)b * pbstride + ((long)s * 2 + m) * maxblk;
+    double t = 0.0;
+    for (int k = 0; k < nblk; ++k) t += p[k];
+    sum[m] = t;
+  }
+  const double pi = 3.14159265358979323846;
+  const double V = L * L * L, dx = L / N;
+  const double C = 4.0 * dx * dx * dx / ((double)n_c * n_c * V * V);
+  const double nk = Nk[s];
+  const double PA = C * C * sum[0] / (V * nk), PB = C * C * sum[1] / (V * nk);
+  const double kc = n_c * 2.0 * pi / L;
+  double* o = out + (long)i * 4;
+  o[0] = PA;
+  o[1] = PB;
+  o[2] = nk;
+  o[3] = kc * kc * kc / (48.0 * pi * pi) * (PA + PB);
+}
+
+#endif
+
+}  // namespace sigw

@@ -1,0 +1,64 @@
+// Host-callable launchers of the device kernels, one instantiation per working
+// precision (float in ops_f32.cu, double in ops_f64.cu).  All pointers are device
+// pointers; each launcher queues work on `st` and returns the launch status.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sigw {
+
+// Tile shapes chosen per (precision, N); exposed so the host can size buffers.
+struct LaunchShape {
+  int tc_strided;   // columns per CTA in strided passes
+  int tc_f3;        // columns per CTA in the forward-axis-0 / TT / bin pass
+  int maxblk_f3;    // upper bound on CTAs of one forward-axis-0 / TT / bin launch
+};
+
+struct MapArgs {
+  int kind;  // 0 gauss, 1 local, 2 usr
+  double F, G, floor;
+};
+
+template <typename T>
+struct OpsRT {
+  // ---- synthesis chain (packed layout [b][a0][a1][N/2], standard layout [b][k0][k1][N/2+1])
+  static cudaError_t rows_r2c_noise(int N, void* Y, const uint64_t* seeds, int batch, const void* tw, cudaStream_t st);
+  static cudaError_t rows_r2c_real(int N, const void* R, void* Y, int batch, const void* tw, cudaStream_t st);
+  static cudaError_t rows_r2c_map(int N, const void* R, void* Y, int batch, MapArgs map, const double* mean,
+                                  unsigned long long* hits, const void* tw, cudaStream_t st);
+  static cudaError_t rows_c2r(int N, const void* Y, void* R, int batch, double scale, double* sq_partial,
+                              const void* tw, cudaStream_t st);
+  static cudaError_t pass(int N, void* Y, int axis, int dir, int batch, const void* tw, cudaStream_t st);
+  // mode 0: times amp[|n|^2] * factor and zero on k = 0 and the Nyquist planes; mode 1: times factor
+  static cudaError_t unpack(int N, const void* Y, void* X, int batch, const void* amp, double factor, int mode,
+                            cudaStream_t st);
+  static cudaError_t pack(int N, const void* X, void* Y, int batch, cudaStream_t st);
+  static int rows_blocks(int N);  // CTAs per realisation of rows_c2r (entries of sq_partial per realisation)
+  static LaunchShape shape(int N);
+
+  // ---- hot path
+  // first inverse pass (axis 0) with the filter phi_a(cell) and the i n_0 gradient factor
+  static cudaError_t p1(int N, const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
+                        int alpha0, int nb, int batch, const void* tw, cudaStream_t st);
+  // second inverse pass (axis 1), three outputs per term
+  static cudaError_t p2(int N, const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
+                        const void* tw, cudaStream_t st);
+  // last inverse pass (axis 2, C2R) + sum_a sigma_a g_i g_j + forward R2C along axis 2 keeping k2 <= n_c
+  static cudaError_t p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
+                        const void* tw, cudaStream_t st);
+  // forward pass along axis 1 keeping |n1| <= n_c
+  static cudaError_t f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st);
+  // forward pass along axis 0 + TT projection + shell sum -> per-CTA FP64 partials
+  static cudaError_t f3(int N, const void* F2, int n_c, double* partial, long pbstride, int batch, const void* tw,
+                        cudaStream_t st);
+};
+
+extern template struct OpsRT<float>;
+extern template struct OpsRT<double>;
+
+// precision-independent kernels (defined in ops_f64.cu)
+cudaError_t launch_reduce_mean(const double* part, int nblk, double* mean, int batch, double inv, cudaStream_t st);
+cudaError_t launch_fin(const double* partial, long pbstride, int maxblk, int n_shells, const int* shells,
+                       const double* Nk, int N, double L, int tc3, double* out, int batch, cudaStream_t st);
+
+}  // namespace sigw

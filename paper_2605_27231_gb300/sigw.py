@@ -1,0 +1,223 @@
+"""ctypes binding of libsigw.so (argument marshalling only; every step runs in the library).
+
+Names follow the C ABI in include/sigw.h.  The binding raises ``SigwError`` for
+every non-OK status and ``RuntimeError`` when the compiled library is missing:
+there is no fallback implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsigw.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ETIMEOUT, EBUSY, ENOTREADY, ESTATE = range(9)
+MAP_GAUSS, MAP_LOCAL, MAP_USR = 0, 1, 2
+MAP_KINDS = {"gauss": MAP_GAUSS, "local": MAP_LOCAL, "usr": MAP_USR}
+
+
+class SigwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("sigw status %d (%s): %s" % (status, _strerror(status), msg))
+        self.status = status
+
+
+class Opts(C.Structure):
+    _fields_ = [("n_modes", C.c_int), ("n_alpha", C.c_int), ("umin", C.c_double), ("umax", C.c_double),
+                ("upiv", C.c_double), ("sigp", C.c_double), ("Ap", C.c_double), ("precision", C.c_int),
+                ("alpha_batch", C.c_int), ("max_batch", C.c_int), ("strict_domain", C.c_int)]
+
+
+class PZeta(C.Structure):
+    _fields_ = [("A", C.c_double), ("sigma", C.c_double), ("kstar", C.c_double)]
+
+
+class NGMap(C.Structure):
+    _fields_ = [("kind", C.c_int), ("F_NL", C.c_double), ("G_NL", C.c_double), ("usr_floor", C.c_double)]
+
+
+_lib = None
+_dbl = C.POINTER(C.c_double)
+_i64 = C.POINTER(C.c_int64)
+
+
+def lib():
+    """Load libsigw.so (built by paper_2605_27231_gb300.build.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsigw.so is not built (%s); call __graft_entry__.build() first" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "sigw_opts_default": (C.c_int, [C.POINTER(Opts)]),
+        "sigw_plan_footprint": (C.c_int, [C.c_int, C.POINTER(Opts), C.POINTER(C.c_size_t)]),
+        "sigw_plan_create": (C.c_int, [C.c_int, C.c_double, C.POINTER(Opts), P, C.POINTER(P)]),
+        "sigw_plan_destroy": (C.c_int, [P]),
+        "sigw_plan_last_error": (C.c_char_p, [P]),
+        "sigw_plan_kernel_terms": (C.c_int, [P, C.c_int, _dbl, _dbl, _dbl]),
+        "sigw_generate": (C.c_int, [P, C.POINTER(PZeta), C.POINTER(NGMap), C.POINTER(C.c_uint64), C.c_int, _i64]),
+        "sigw_spectrum": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, _dbl, _dbl, _dbl, _i64]),
+        "sigw_spectrum_async": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, P]),
+        "sigw_copy_phi": (C.c_int, [P, C.c_int, P]),
+        "sigw_fft3d": (C.c_int, [P, C.c_int, P, P]),
+        "sigw_synchronize": (C.c_int, [P]),
+        "sigw_strerror": (C.c_char_p, [C.c_int]),
+        "sigw_decompose": (C.c_int, [C.POINTER(Opts), C.c_int, _dbl, _dbl, _dbl, _dbl]),
+        "sigw_cell_table": (C.c_int, [C.POINTER(Opts), C.c_int, C.c_int, C.POINTER(C.c_int16)]),
+        "sigw_debug_fail_alloc": (C.c_int, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _strerror(s):
+    try:
+        return lib().sigw_strerror(s).decode()
+    except Exception:
+        return "?"
+
+
+def _check(status, plan=None, what=""):
+    if status != OK:
+        msg = what
+        if plan is not None:
+            msg += ": " + lib().sigw_plan_last_error(plan).decode()
+        raise SigwError(status, msg)
+
+
+def default_opts(**over):
+    o = Opts()
+    _check(lib().sigw_opts_default(C.byref(o)))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def decompose(m, opts=None, all_sigma=False):
+    """Host-only decomposition: (sigma[n_alpha], phi[n_alpha, n_modes], edges[n_modes+1], sigma_all or None)."""
+    o = opts or default_opts()
+    sigma = np.zeros(o.n_alpha)
+    phi = np.zeros((o.n_alpha, o.n_modes))
+    edges = np.zeros(o.n_modes + 1)
+    sall = np.zeros(o.n_modes) if all_sigma else None
+    _check(lib().sigw_decompose(C.byref(o), m, _ptr(sigma, C.c_double), _ptr(phi, C.c_double),
+                                _ptr(edges, C.c_double), _ptr(sall, C.c_double) if all_sigma else None))
+    return sigma, phi, edges, sall
+
+
+def cell_table(n_c, msq_max, opts=None):
+    o = opts or default_opts()
+    lut = np.zeros(msq_max + 1, dtype=np.int16)
+    _check(lib().sigw_cell_table(C.byref(o), n_c, msq_max, _ptr(lut, C.c_int16)))
+    return lut
+
+
+def footprint(N, opts=None):
+    o = opts or default_opts()
+    n = C.c_size_t(0)
+    _check(lib().sigw_plan_footprint(N, C.byref(o), C.byref(n)))
+    return n.value
+
+
+def debug_fail_alloc(n):
+    _check(lib().sigw_debug_fail_alloc(n))
+
+
+class Plan:
+    """A lattice (N, L) with its decomposition, tables and device buffers (sigw_plan_create)."""
+
+    def __init__(self, N, L, opts=None, stream=None, **over):
+        self.opts = opts or default_opts(**over)
+        self.N, self.L = N, L
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        _check(lib().sigw_plan_create(N, L, C.byref(self.opts), st, C.byref(h)), None, "sigw_plan_create")
+        self._h = h
+        self.batch = 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sigw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def dtype(self):
+        return np.complex128 if self.opts.precision == 64 else np.complex64
+
+    def kernel_terms(self, m):
+        o = self.opts
+        sigma, phi, edges = np.zeros(o.n_alpha), np.zeros((o.n_alpha, o.n_modes)), np.zeros(o.n_modes + 1)
+        _check(lib().sigw_plan_kernel_terms(self._h, m, _ptr(sigma, C.c_double), _ptr(phi, C.c_double),
+                                            _ptr(edges, C.c_double)), self._h, "kernel_terms")
+        return sigma, phi, edges
+
+    def generate(self, A, sigma, kstar, kind="gauss", F_NL=0.0, G_NL=0.0, usr_floor=1e-6, seeds=(1,)):
+        """sigw_generate; returns the USR floor-hit counts per realisation."""
+        pz = PZeta(A, sigma, kstar)
+        mp = NGMap(MAP_KINDS[kind] if isinstance(kind, str) else kind, F_NL, G_NL, usr_floor)
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        hits = np.zeros(len(sd), dtype=np.int64)
+        _check(lib().sigw_generate(self._h, C.byref(pz), C.byref(mp), _ptr(sd, C.c_uint64), len(sd),
+                                   _ptr(hits, C.c_int64)), self._h, "sigw_generate")
+        self.batch = len(sd)
+        return hits
+
+    def generate_spec(self, spec, seeds=None):
+        return self.generate(spec.A, spec.sigma, spec.kstar, spec.kind, spec.F_NL, spec.G_NL, spec.usr_floor,
+                             seeds=(spec.seed,) if seeds is None else seeds)
+
+    def spectrum(self, shells=None):
+        """sigw_spectrum; dict of [batch, n_shells] arrays: omega, PA, PB, Nk (and n_c)."""
+        sh = np.arange(1, self.N // 2 + 1, dtype=np.int32) if shells is None else np.ascontiguousarray(shells, dtype=np.int32)
+        ns = len(sh)
+        out = {k: np.zeros((self.batch, ns)) for k in ("omega", "PA", "PB")}
+        nk = np.zeros((self.batch, ns), dtype=np.int64)
+        _check(lib().sigw_spectrum(self._h, _ptr(sh, C.c_int), ns, _ptr(out["omega"], C.c_double),
+                                   _ptr(out["PA"], C.c_double), _ptr(out["PB"], C.c_double), _ptr(nk, C.c_int64)),
+               self._h, "sigw_spectrum")
+        out["Nk"] = nk
+        out["n_c"] = sh
+        return out
+
+    def spectrum_async(self, dev_out_ptr, shells=None):
+        sh = np.arange(1, self.N // 2 + 1, dtype=np.int32) if shells is None else np.ascontiguousarray(shells, dtype=np.int32)
+        _check(lib().sigw_spectrum_async(self._h, _ptr(sh, C.c_int), len(sh), C.c_void_p(dev_out_ptr)), self._h,
+               "sigw_spectrum_async")
+
+    def copy_phi(self, b=0):
+        out = np.zeros((self.N, self.N, self.N // 2 + 1), dtype=self.dtype)
+        _check(lib().sigw_copy_phi(self._h, b, out.ctypes.data_as(C.c_void_p)), self._h, "sigw_copy_phi")
+        return out
+
+    def fft3d(self, direction, in_ptr, out_ptr):
+        _check(lib().sigw_fft3d(self._h, direction, C.c_void_p(in_ptr), C.c_void_p(out_ptr)), self._h, "sigw_fft3d")
+
+    def synchronize(self):
+        _check(lib().sigw_synchronize(self._h), self._h, "sigw_synchronize")

@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle, element by element.
+
+Tolerances: FP64 path rtol 1e-9 per shell (round-off of different summation orders);
+FP32 path rtol 1e-4 per shell, the stated bound for FP32 fields/FFTs against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import decomposition as odec
+from oracle import sigw as osigw
+from oracle import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {64: 1e-9, 32: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_27231_gb300 import build, sigw
+    build.build()
+    sigw.lib()
+    return sigw
+
+
+@pytest.fixture(scope="module")
+def dec():
+    return odec.build()
+
+
+def _oracle(spec, dec, shells):
+    Phi, hits = synth.phi_tilde(spec.N, spec.L, spec.A, spec.sigma, spec.kstar, spec.seed, spec.kind, spec.F_NL,
+                                spec.G_NL, spec.usr_floor)
+    return osigw.omega(Phi, spec.L, dec, shells=shells), Phi, hits
+
+
+def _gpu(lib, spec, shells, precision, **opts):
+    with lib.Plan(spec.N, spec.L, precision=precision, **opts) as p:
+        hits = p.generate_spec(spec)
+        out = p.spectrum(shells)
+        phi = p.copy_phi(0)
+    return out, phi, hits
+
+
+# ------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_fft3d_matches_numpy(lib, N, precision):
+    import torch
+    rdt = torch.float64 if precision == 64 else torch.float32
+    cdt = torch.complex128 if precision == 64 else torch.complex64
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((N, N, N))
+    with lib.Plan(N, 1.0, precision=precision, n_alpha=2) as p:
+        xd = torch.tensor(x, dtype=rdt, device="cuda")
+        Xd = torch.empty((N, N, N // 2 + 1), dtype=cdt, device="cuda")
+        p.fft3d(-1, xd.data_ptr(), Xd.data_ptr())
+        p.synchronize()
+        X = Xd.cpu().numpy()
+        ref = np.fft.rfftn(x)
+        tol = 1e-12 if precision == 64 else 2e-6
+        assert np.abs(X - ref).max() <= tol * np.abs(ref).max() * np.sqrt(np.log2(N ** 3))
+        yd = torch.empty((N, N, N), dtype=rdt, device="cuda")
+        p.fft3d(+1, Xd.data_ptr(), yd.data_ptr())
+        p.synchronize()
+        y = yd.cpu().numpy() / N ** 3
+        assert np.abs(y - x).max() <= tol * 10 * np.abs(x).max()
+
+
+# ------------------------------------------------------------------ synthesis
+@pytest.mark.parametrize("kind,F", [("gauss", 0.0), ("local", 3.0), ("usr", 0.0)])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_phi_matches_oracle(lib, dec, kind, F, precision):
+    spec = workloads.Spec(N=32, L=1.0, A=1e-2, sigma=0.5, kstar=8 * 2 * np.pi, kind=kind, F_NL=F, seed=3)
+    Phi, hits = synth.phi_tilde(spec.N, spec.L, spec.A, spec.sigma, spec.kstar, spec.seed, kind, F)
+    with lib.Plan(spec.N, spec.L, precision=precision, n_alpha=2) as p:
+        ghits = p.generate_spec(spec)
+        phi = p.copy_phi(0)
+    ref = Phi[:, :, :spec.N // 2 + 1]
+    tol = 1e-12 if precision == 64 else 3e-6
+    assert np.abs(phi - ref).max() <= tol * np.abs(ref).max()
+    if precision == 64:
+        assert int(ghits[0]) == hits
+
+
+# ------------------------------------------------------------------ full spectra, small lattices
+@pytest.mark.parametrize("N", [8, 16])
+@pytest.mark.parametrize("kind,F", [("gauss", 0.0), ("local", 3.0), ("usr", 0.0)])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_omega_all_shells_small(lib, dec, N, kind, F, precision):
+    spec = workloads.Spec(N=N, L=1.0, A=2e-2, sigma=0.5, kstar=(N // 4) * 2 * np.pi, kind=kind, F_NL=F, seed=11)
+    ref, _, _ = _oracle(spec, dec, None)
+    got, _, _ = _gpu(lib, spec, None, precision)
+    np.testing.assert_array_equal(got["Nk"][0], ref["Nk"])
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=RTOL[precision])
+    np.testing.assert_allclose(got["PA"][0], ref["PA"], rtol=RTOL[precision])
+    np.testing.assert_allclose(got["PB"][0], ref["PB"], rtol=RTOL[precision])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_omega_gauss32_all_shells(lib, dec, precision):
+    """The 32^3 Gaussian workload (log-normal A = 1e-2, sigma = 0.5, k* = 8 k_f), every shell."""
+    spec = workloads.workload("gauss32")
+    ref, _, _ = _oracle(spec, dec, None)
+    got, _, _ = _gpu(lib, spec, None, precision)
+    np.testing.assert_array_equal(got["Nk"][0], ref["Nk"])
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=RTOL[precision])
+
+
+def test_omega_64_local_fp32(lib, dec):
+    spec = workloads.scaled(workloads.workload("local128"), 64)
+    shells = [1, 2, 7, 8, 9, 16, 31, 32]
+    ref, _, _ = _oracle(spec, dec, shells)
+    got, _, _ = _gpu(lib, spec, shells, 32)
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=1e-4)
+
+
+def test_odd_alpha_and_small_batches(lib, dec):
+    """An odd number of terms (the last pair has one member) and an alpha batch that does not divide it."""
+    spec = workloads.Spec(N=16, L=2.0, A=1e-2, sigma=0.7, kstar=3 * np.pi, kind="local", F_NL=-1.2, seed=5)
+    shells = [1, 4, 8]
+    d = odec.build(n_alpha=7)
+    ref, _, _ = _oracle(spec, d, shells)
+    got, _, _ = _gpu(lib, spec, shells, 64, n_alpha=7, alpha_batch=3)
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=1e-9)
+
+
+def test_batch_equals_single_bitwise(lib):
+    """Four seeds in one call give the bits of four single-seed calls."""
+    spec = workloads.scaled(workloads.workload("usr256"), 32)
+    seeds = [1, 2, 3, 4]
+    shells = [2, 4, 9, 16]
+    with lib.Plan(spec.N, spec.L, precision=32, max_batch=4) as p:
+        p.generate_spec(spec, seeds=seeds)
+        batched = p.spectrum(shells)["omega"]
+    for i, s in enumerate(seeds):
+        with lib.Plan(spec.N, spec.L, precision=32) as p:
+            p.generate_spec(spec, seeds=[s])
+            single = p.spectrum(shells)["omega"][0]
+        assert np.array_equal(batched[i], single)
+
+
+def test_state_errors(lib):
+    with lib.Plan(16, 1.0, n_alpha=2) as p:
+        with pytest.raises(lib.SigwError) as e:
+            p.spectrum()
+        assert e.value.status == lib.ESTATE
+        p.generate(1e-2, 0.5, 4 * 2 * np.pi)
+        with pytest.raises(lib.SigwError) as e:
+            p.spectrum([0])
+        assert e.value.status == lib.EINVAL
+        with pytest.raises(lib.SigwError) as e:
+            p.spectrum([9])
+        assert e.value.status == lib.EINVAL
+
+
+def test_injected_allocation_failure_reports_enomem(lib):
+    lib.debug_fail_alloc(3)
+    try:
+        with pytest.raises(lib.SigwError) as e:
+            lib.Plan(16, 1.0, n_alpha=2)
+        assert e.value.status == lib.ENOMEM
+    finally:
+        lib.debug_fail_alloc(0)
+    with lib.Plan(16, 1.0, n_alpha=2) as p:  # the library is usable afterwards
+        p.generate(1e-2, 0.5, 4 * 2 * np.pi)
+        assert np.all(np.isfinite(p.spectrum()["omega"]))
+
+
+def test_usr_strict_mode(lib):
+    spec = workloads.Spec(N=16, L=1.0, A=5e-1, sigma=0.5, kstar=4 * 2 * np.pi, kind="usr", seed=2)
+    with lib.Plan(16, 1.0, n_alpha=2, strict_domain=1, precision=64) as p:
+        with pytest.raises(lib.SigwError) as e:
+            p.generate_spec(spec)
+        assert e.value.status == lib.EDOMAIN
+    _, hits = synth.phi_tilde(spec.N, spec.L, spec.A, spec.sigma, spec.kstar, spec.seed, "usr")
+    assert hits > 0
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled shells
+@pytest.mark.slow
+def test_local128_sampled_shells_fp32(lib, dec):
+    """The 128^3 local f_NL = 5 workload in the bench's launch configuration, sampled shells."""
+    spec = workloads.workload("local128")
+    shells = [1, 16, 33, 64]
+    ref, _, _ = _oracle(spec, dec, shells)
+    got, _, _ = _gpu(lib, spec, shells, 32)
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=1e-4)
+
+
+@pytest.mark.slow
+def test_usr256_sampled_shell_fp32(lib, dec):
+    """The 256^3 USR-tail workload (A = 5e-3, sigma = 0.3, k* = 32 k_f) at the spectral peak, FP32."""
+    spec = workloads.workload("usr256")
+    shells = [32]
+    ref, _, hits = _oracle(spec, dec, shells)
+    got, _, ghits = _gpu(lib, spec, shells, 32)
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=1e-4)
+    assert abs(int(ghits[0]) - hits) <= max(2, hits // 100)
