@@ -1,0 +1,300 @@
+"""Benchmark: SIGW spectra/s at 256^3 (FP32 path, FP64 path on the same GPU), one JSON line.
+
+A step is one pass of the whole hot path over one batch of realisations of the
+256^3 USR-tail workload (log-normal A = 5e-3, sigma = 0.3, k* = 32 k_f; 4 seeds per
+step): Philox synthesis, the USR map, and all 128 target shells of the
+FFT-convolution envelopes, TT projection and binning.  One spectrum = Omega_GW in all
+N/2 shells for one seed.
+
+  value : spectra/s with the work queued through sigw_generate + sigw_spectrum_async
+          (parameters in, results left in HBM); device time from CUDA events on the
+          library's stream, max over ranks.
+  e2e   : the same through sigw_generate + sigw_spectrum (host seeds in, host Omega out),
+          host copies inside the timed region.
+Every rank processes its own seeds (no collective on the data path): "scaling": "weak".
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same workload
+(one target shell, a few separable terms) and extrapolates to spectra/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2605_27231_gb300 import sigw
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    spec = workloads.workload(args.workload)
+    batch = args.batch
+    seeds = [spec.seed + 1000 * rank + i for i in range(batch)] if args.workload != "usr256" else \
+        [s + 1000 * rank for s in workloads.USR256_SEEDS][:batch]
+    stream = torch.cuda.Stream()
+    plan = sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=32, max_batch=batch)
+    n_sh = spec.N // 2
+    dev_out = torch.empty(batch * n_sh * 4, dtype=torch.float64, device="cuda")
+
+    def step():
+        plan.generate_spec(spec, seeds=seeds)
+        plan.spectrum_async(dev_out.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    plan.synchronize()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region (events on the library's stream) + per-kernel events
+    clk = Clocks(local)
+    barrier()
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    prof = plan.profile_read()
+    plan.profile(False)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * batch * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    barrier()
+    plan.profile(False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.generate_spec(spec, seeds=seeds)
+        res = plan.spectrum()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    io = plan.profile_read()
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * batch * args.steps / float(t.item())
+    omega_ok = bool(np.all(np.isfinite(res["omega"])) and np.all(res["omega"] > 0))
+
+    # ---- dominant kernel roofline
+    peaks, pk_src = _peaks()
+    kinds = [k for k in sigw.KINDS if prof[k]["launches"]]
+    dom = max(kinds, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    kernels = {k: {"ms_per_step": prof[k]["ms"] / args.steps, "launches_per_step": prof[k]["launches"] / args.steps,
+                   "GBps": (prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9) if prof[k]["ms"] > 0 else None}
+               for k in kinds}
+    launches = sum(prof[k]["launches"] for k in sigw.KINDS)
+    plan.close()
+
+    # ---- FP64 path on the same GPU (sampled shells, extrapolated to a spectrum)
+    fp64 = None
+    if rank == 0 and args.fp64_shells > 0:
+        with sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=64, max_batch=1) as p64:
+            shells = np.unique(np.linspace(1, n_sh, args.fp64_shells).astype(np.int32))
+            p64.generate_spec(spec, seeds=seeds[:1])
+            p64.spectrum(shells[:1])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p64.generate_spec(spec, seeds=seeds[:1])
+            b.record(stream)
+            b.synchronize()
+            gen_ms = a.elapsed_time(b)
+            a.record(stream)
+            p64.spectrum_async(dev_out.data_ptr(), shells)
+            b.record(stream)
+            b.synchronize()
+            sh_ms = b and a.elapsed_time(b)
+        per_spec_s = (gen_ms + sh_ms * n_sh / len(shells)) / 1e3
+        fp64 = {"value": 1.0 / per_spec_s, "unit": "spectra/s", "dtype": "f64",
+                "sample": "1 seed, shells %s of 1..%d, extrapolated to all shells" % (shells.tolist(), n_sh),
+                "fp32_over_fp64": (value / ws) / (1.0 / per_spec_s)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(spec, args.cpu_terms)
+
+    if rank == 0:
+        line = {
+            "metric": "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path)",
+            "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
+            "config": {"workload": args.workload, "N": spec.N, "L": spec.L, "A": spec.A, "sigma": spec.sigma,
+                       "kstar_over_kf": round(spec.kstar * spec.L / (2 * 3.141592653589793), 6), "map": spec.kind,
+                       "seeds_per_step": batch, "shells": n_sh, "n_alpha": 50, "n_modes": 200,
+                       "l2": "inputs larger than L2 (%.1f GB device working set per step)" % (sigw.footprint(
+                           spec.N, sigw.default_opts(max_batch=batch)) / 1e9),
+                       "parallelism": "replicas, seeds sharded across ranks"},
+            "e2e": {"value": e2e_value, "unit": "spectra/s", "h2d_bytes_per_step": io["h2d_bytes"] / args.steps,
+                    "d2h_bytes_per_step": io["d2h_bytes"] / args.steps},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": pk_src + " (copy)"},
+            "kernels": kernels,
+            "clocks": clocks,
+            "fp64_path": fp64,
+            "cpu_baseline": cpu,
+            "omega_finite_positive": omega_ok,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def oracle_sample(spec, n_terms):
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload: synthesis of one realisation
+    and one target shell (n_c = N/8) of one kernel with n_terms and 2 n_terms separable terms; the per-term
+    and fixed costs are extrapolated to all shells, both kernels and 50 terms."""
+    import numpy as np
+    from oracle import decomposition, sigw as osigw, synth
+    dec = decomposition.build()
+    t0 = time.perf_counter()
+    Phi, _ = synth.phi_tilde(spec.N, spec.L, spec.A, spec.sigma, spec.kstar, spec.seed, spec.kind, spec.F_NL,
+                             spec.G_NL, spec.usr_floor)
+    t_syn = time.perf_counter() - t0
+    n_c = spec.N // 8
+    ts = []
+    for nt in (n_terms, 2 * n_terms):
+        t0 = time.perf_counter()
+        osigw.envelope_fields(Phi, spec.L, dec.edges, dec.sigma["s"][:nt], dec.phi["s"][:nt], n_c)
+        ts.append(time.perf_counter() - t0)
+    per_term = (ts[1] - ts[0]) / n_terms
+    fixed = max(ts[0] - n_terms * per_term, 0.0)
+    per_spec = t_syn + (spec.N // 2) * 2 * (fixed + 50 * per_term)
+    return {"value": 1.0 / per_spec, "unit": "spectra/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "N=%d: synthesis + shell n_c=%d, kernel I_s, %d and %d terms (%.1f s of CPU); "
+                      "extrapolated to %d shells x 2 kernels x 50 terms" % (spec.N, n_c, n_terms, 2 * n_terms,
+                                                                            t_syn + sum(ts), spec.N // 2),
+            "seconds_per_spectrum": per_spec}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    spec = workloads.workload(args.workload)
+    vals = []
+    t_start = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(spec, args.cpu_terms)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.mean(x["value"] for x in vals)
+    wall = time.perf_counter() - t_start
+    line = {"impl": "reference", "metric": "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path)",
+            "value": v, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / (args.warmup + args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
+            "config": {"workload": args.workload, "N": spec.N},
+            "cpu_baseline": {"value": v, "unit": "spectra/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="usr256")
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--fp64-shells", type=int, default=4)
+    ap.add_argument("--cpu-terms", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

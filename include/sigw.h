@@ -149,6 +149,24 @@ sigw_status sigw_synchronize(sigw_plan plan);
 /* Human-readable text of a status code. */
 const char* sigw_strerror(sigw_status s);
 
+/* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter),
+ * 2 second inverse pass, 3 last inverse pass + product + first forward pass, 4 second forward pass,
+ * 5 last forward pass + TT projection + shell sum, 6 bin finalisation. */
+#define SIGW_NKINDS 7
+typedef struct sigw_profile {
+  double ms[SIGW_NKINDS];        /* summed CUDA-event durations (only while event timing is on) */
+  double bytes[SIGW_NKINDS];     /* algorithmic bytes: each input element read once, each output written once */
+  int64_t launches[SIGW_NKINDS]; /* kernel launches (always counted) */
+  double h2d_bytes, d2h_bytes;   /* host<->device bytes copied by the library */
+} sigw_profile;
+
+/* enable != 0: bracket every kernel launch with CUDA events on the plan's stream (adds a few microseconds
+ * per launch).  Both enabling and disabling reset the counters. */
+sigw_status sigw_plan_profile(sigw_plan plan, int enable);
+
+/* Wait for the plan's stream, fill *out with the counters accumulated since the last reset, and reset them. */
+sigw_status sigw_plan_profile_read(sigw_plan plan, sigw_profile* out);
+
 /* Host-only (no GPU needed): the truncated decomposition a plan with these options uses, for kernel m
  * (0: I_s, 1: I_c).  Same outputs as sigw_plan_kernel_terms; opts may be NULL (defaults).
  * Also reports all n_modes eigenvalues (sigma_all[n_modes], sorted by |sigma| descending) when non-NULL. */

@@ -114,6 +114,17 @@ struct sigw_plan_s {
   uint64_t* d_seeds = nullptr;
   int generated = 0;
   std::string err;
+  // accounting (see sigw_profile)
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  long long launches[SIGW_NKINDS] = {0};
+  double kbytes[SIGW_NKINDS] = {0};
+  double h2d = 0, d2h = 0;
 
   size_t relem() const { return opts.precision == 64 ? 8 : 4; }
   size_t celem() const { return 2 * relem(); }
@@ -136,6 +147,63 @@ sigw_status cuda_fail(sigw_plan p, cudaError_t e, const char* what) {
   do {                                                   \
     cudaError_t _e = (call);                             \
     if (_e != cudaSuccess) return cuda_fail(plan, _e, what); \
+  } while (0)
+
+cudaEvent_t get_event(sigw_plan p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void prof_reset(sigw_plan p) {
+  for (auto& r : p->recs) {
+    p->pool.push_back(r.a);
+    p->pool.push_back(r.b);
+  }
+  p->recs.clear();
+  for (int k = 0; k < SIGW_NKINDS; ++k) {
+    p->launches[k] = 0;
+    p->kbytes[k] = 0;
+  }
+  p->h2d = p->d2h = 0;
+}
+
+// Launch one kernel (the callable returns its launch status) with accounting of kind / algorithmic bytes.
+template <typename F>
+sigw_status run(sigw_plan p, int kind, double bytes, const char* what, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (p->prof_on) {
+    a = get_event(p);
+    if (a) cudaEventRecord(a, p->st);
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return cuda_fail(p, e, what);
+  if (p->prof_on && a) {
+    b = get_event(p);
+    if (b) {
+      cudaEventRecord(b, p->st);
+      p->recs.push_back({kind, a, b});
+    } else {
+      p->pool.push_back(a);
+    }
+  }
+  p->launches[kind] += 1;
+  p->kbytes[kind] += bytes;
+  return SIGW_OK;
+}
+
+#define RUN(plan, kind, bytes, what, expr)                                       \
+  do {                                                                            \
+    sigw_status _s = run(plan, kind, (double)(bytes), what, [&]() { return (expr); }); \
+    if (_s != SIGW_OK) return _s;                                                 \
   } while (0)
 
 sigw_status dev_alloc(sigw_plan p, void** ptr, size_t bytes) {
@@ -370,6 +438,8 @@ sigw_status sigw_plan_destroy(sigw_plan p) {
   if (!p) return SIGW_OK;
   if (p->st) cudaStreamSynchronize(p->st);
   for (void* q : p->allocs) cudaFree(q);
+  prof_reset(p);
+  for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
   (void)cudaGetLastError();
   delete p;
@@ -425,31 +495,37 @@ sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* m
   void* X = work + (size_t)p->opts.max_batch * NN * H * cel;
   void* R = (char*)X + (size_t)p->opts.max_batch * NN * (H + 1) * cel;
   cudaStream_t st = p->st;
-  CKP(p, OPS(p, rows_r2c_noise, N, Y, p->d_seeds, batch, p->d_tw, st), "noise + rows R2C");
-  CKP(p, OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st), "forward axis 1");
-  CKP(p, OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st), "forward axis 0");
+  const double Yb = (double)batch * NN * H * cel, Xb = (double)batch * NN * (H + 1) * cel;
+  const double Rb = (double)batch * NN * N * p->relem();
+  p->h2d += buf.size() + sizeof(uint64_t) * batch;
+  RUN(p, 0, Yb, "noise + rows R2C", OPS(p, rows_r2c_noise, N, Y, p->d_seeds, batch, p->d_tw, st));
+  RUN(p, 0, 2 * Yb, "forward axis 1", OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st));
+  RUN(p, 0, 2 * Yb, "forward axis 0", OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st));
   if (map->kind == SIGW_MAP_GAUSS) {
-    CKP(p, OPS(p, unpack, N, Y, p->d_phi, batch, p->d_amp, 2.0 / 3.0, 0, st), "unpack (Gaussian Phi)");
+    RUN(p, 0, Yb + Xb, "unpack (Gaussian Phi)", OPS(p, unpack, N, Y, p->d_phi, batch, p->d_amp, 2.0 / 3.0, 0, st));
   } else {
-    CKP(p, OPS(p, unpack, N, Y, X, batch, p->d_amp, 1.0, 0, st), "unpack (zeta_g)");
-    CKP(p, OPS(p, pack, N, X, Y, batch, st), "pack");
-    CKP(p, OPS(p, pass, N, Y, 0, +1, batch, p->d_tw, st), "inverse axis 0");
-    CKP(p, OPS(p, pass, N, Y, 1, +1, batch, p->d_tw, st), "inverse axis 1");
+    RUN(p, 0, Yb + Xb, "unpack (zeta_g)", OPS(p, unpack, N, Y, X, batch, p->d_amp, 1.0, 0, st));
+    RUN(p, 0, Yb + Xb, "pack", OPS(p, pack, N, X, Y, batch, st));
+    RUN(p, 0, 2 * Yb, "inverse axis 0", OPS(p, pass, N, Y, 0, +1, batch, p->d_tw, st));
+    RUN(p, 0, 2 * Yb, "inverse axis 1", OPS(p, pass, N, Y, 1, +1, batch, p->d_tw, st));
     const double scale = 1.0 / ((double)NN * N * dx * dx * dx);
-    CKP(p, OPS(p, rows_c2r, N, Y, R, batch, scale, p->d_sq, p->d_tw, st), "rows C2R (zeta_g)");
+    RUN(p, 0, Yb + Rb, "rows C2R (zeta_g)", OPS(p, rows_c2r, N, Y, R, batch, scale, p->d_sq, p->d_tw, st));
     const int rb = OPS(p, rows_blocks, N);
-    CKP(p, sigw::launch_reduce_mean(p->d_sq, rb, p->d_mean, batch, 1.0 / ((double)NN * N), st), "mean zeta_g^2");
+    RUN(p, 0, (double)batch * rb * 8, "mean zeta_g^2",
+        sigw::launch_reduce_mean(p->d_sq, rb, p->d_mean, batch, 1.0 / ((double)NN * N), st));
     CKP(p, cudaMemsetAsync(p->d_hits, 0, sizeof(unsigned long long) * batch, st), "memset hits");
     sigw::MapArgs ma{map->kind, map->F_NL, map->G_NL, floor};
-    CKP(p, OPS(p, rows_r2c_map, N, R, Y, batch, ma, p->d_mean, p->d_hits, p->d_tw, st), "map + rows R2C");
-    CKP(p, OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st), "forward axis 1");
-    CKP(p, OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st), "forward axis 0");
-    CKP(p, OPS(p, unpack, N, Y, p->d_phi, batch, nullptr, (2.0 / 3.0) * dx * dx * dx, 1, st), "unpack (Phi)");
+    RUN(p, 0, Rb + Yb, "map + rows R2C", OPS(p, rows_r2c_map, N, R, Y, batch, ma, p->d_mean, p->d_hits, p->d_tw, st));
+    RUN(p, 0, 2 * Yb, "forward axis 1", OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st));
+    RUN(p, 0, 2 * Yb, "forward axis 0", OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st));
+    RUN(p, 0, Yb + Xb, "unpack (Phi)", OPS(p, unpack, N, Y, p->d_phi, batch, nullptr, (2.0 / 3.0) * dx * dx * dx, 1, st));
   }
   std::vector<unsigned long long> hits(batch, 0);
-  if (map->kind == SIGW_MAP_USR)
+  if (map->kind == SIGW_MAP_USR) {
     CKP(p, cudaMemcpyAsync(hits.data(), p->d_hits, sizeof(unsigned long long) * batch, cudaMemcpyDeviceToHost, st),
         "download hits");
+    p->d2h += sizeof(unsigned long long) * batch;
+  }
   CKP(p, cudaStreamSynchronize(st), "synthesis");
   p->generated = batch;
   bool any = false;
@@ -488,25 +564,37 @@ sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, do
   void* Ta = p->d_T;
   void* Tb = (char*)p->d_T + (size_t)batch * p->B * NN * H * cel;
   const long pbs = (long)ns * 2 * p->sz.maxblk;
+  p->h2d += sizeof(int) * ns + sizeof(double) * ns;
+  const double fieldb = (double)batch * NN * H * cel;  // one packed complex field per realisation batch
+  const double phib = (double)batch * NN * (H + 1) * cel;
   for (int si = 0; si < ns; ++si) {
     const int n_c = sh[si];
     const int16_t* lut = p->d_lut + (size_t)(n_c - 1) * (p->msq_max + 1);
+    const int ncp = n_c + 1;
+    const int n1lo = std::max(-n_c, -H + 1), nk1 = std::min(n_c, H) - n1lo + 1;
+    // columns (n1, n2) of the F3 pass that reach the shell: n1^2 + n2^2 <= n_c^2 + n_c
+    long disk = 0;
+    for (int n1 = n1lo; n1 < n1lo + nk1; ++n1)
+      for (int n2 = 0; n2 <= n_c; ++n2) disk += (n1 * n1 + n2 * n2 <= n_c * n_c + n_c);
     for (int m = 0; m < 2; ++m) {
       for (int a0 = 0; a0 < n_alpha; a0 += p->B) {
         const int nb = std::min(p->B, n_alpha - a0);
-        CKP(p, OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, st), "P1");
-        CKP(p, OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, st), "P2");
+        RUN(p, 1, phib + 2.0 * nb * fieldb, "P1",
+            OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, st));
+        RUN(p, 2, 5.0 * nb * fieldb, "P2", OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, st));
       }
-      CKP(p, OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, st), "P3");
-      CKP(p, OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st), "F2");
-      CKP(p, OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st),
-          "F3");
+      RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
+          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, st));
+      RUN(p, 4, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
+          OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st));
+      RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3",
+          OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st));
     }
   }
   const sigw::LaunchShape shp = OPS(p, shape, N);
-  CKP(p, sigw::launch_fin(p->d_partial, pbs, p->sz.maxblk, ns, p->d_shells, p->d_Nk, N, p->L, shp.tc_f3,
-                          dev_out ? dev_out : p->d_out, batch, st),
-      "bin finalise");
+  RUN(p, 6, (double)batch * ns * 2 * p->sz.maxblk * 8, "bin finalise",
+      sigw::launch_fin(p->d_partial, pbs, p->sz.maxblk, ns, p->d_shells, p->d_Nk, N, p->L, shp.tc_f3,
+                       dev_out ? dev_out : p->d_out, batch, st));
   return SIGW_OK;
 }
 
@@ -520,6 +608,7 @@ sigw_status sigw_spectrum(sigw_plan p, const int* shells, int n_shells, double* 
   std::vector<double> host((size_t)batch * ns * 4);
   CKP(p, cudaMemcpyAsync(host.data(), p->d_out, host.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st),
       "download results");
+  p->d2h += host.size() * sizeof(double);
   CKP(p, cudaStreamSynchronize(p->st), "spectrum");
   for (int i = 0; i < batch * ns; ++i) {
     if (PA) PA[i] = host[4 * i + 0];
@@ -549,16 +638,45 @@ sigw_status sigw_fft3d(sigw_plan p, int direction, const void* in_dev, void* out
   void* Y = p->d_work;
   cudaStream_t st = p->st;
   if (direction < 0) {
-    CKP(p, OPS(p, rows_r2c_real, N, in_dev, Y, 1, p->d_tw, st), "rows R2C");
-    CKP(p, OPS(p, pass, N, Y, 1, -1, 1, p->d_tw, st), "forward axis 1");
-    CKP(p, OPS(p, pass, N, Y, 0, -1, 1, p->d_tw, st), "forward axis 0");
-    CKP(p, OPS(p, unpack, N, Y, out_dev, 1, nullptr, 1.0, 1, st), "unpack");
+    RUN(p, 0, 0, "rows R2C", OPS(p, rows_r2c_real, N, in_dev, Y, 1, p->d_tw, st));
+    RUN(p, 0, 0, "forward axis 1", OPS(p, pass, N, Y, 1, -1, 1, p->d_tw, st));
+    RUN(p, 0, 0, "forward axis 0", OPS(p, pass, N, Y, 0, -1, 1, p->d_tw, st));
+    RUN(p, 0, 0, "unpack", OPS(p, unpack, N, Y, out_dev, 1, nullptr, 1.0, 1, st));
   } else {
-    CKP(p, OPS(p, pack, N, in_dev, Y, 1, st), "pack");
-    CKP(p, OPS(p, pass, N, Y, 0, +1, 1, p->d_tw, st), "inverse axis 0");
-    CKP(p, OPS(p, pass, N, Y, 1, +1, 1, p->d_tw, st), "inverse axis 1");
-    CKP(p, OPS(p, rows_c2r, N, Y, out_dev, 1, 1.0, nullptr, p->d_tw, st), "rows C2R");
+    RUN(p, 0, 0, "pack", OPS(p, pack, N, in_dev, Y, 1, st));
+    RUN(p, 0, 0, "inverse axis 0", OPS(p, pass, N, Y, 0, +1, 1, p->d_tw, st));
+    RUN(p, 0, 0, "inverse axis 1", OPS(p, pass, N, Y, 1, +1, 1, p->d_tw, st));
+    RUN(p, 0, 0, "rows C2R", OPS(p, rows_c2r, N, Y, out_dev, 1, 1.0, nullptr, p->d_tw, st));
   }
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_profile(sigw_plan p, int enable) {
+  if (!p) return SIGW_EINVAL;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  CKP(p, cudaStreamSynchronize(p->st), "profile");
+  prof_reset(p);
+  p->prof_on = enable != 0;
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_profile_read(sigw_plan p, sigw_profile* out) {
+  if (!p || !out) return SIGW_EINVAL;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  CKP(p, cudaStreamSynchronize(p->st), "profile read");
+  std::memset(out, 0, sizeof(*out));
+  for (auto& r : p->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) out->ms[r.kind] += ms;
+    (void)cudaGetLastError();
+  }
+  for (int k = 0; k < SIGW_NKINDS; ++k) {
+    out->bytes[k] = p->kbytes[k];
+    out->launches[k] = p->launches[k];
+  }
+  out->h2d_bytes = p->h2d;
+  out->d2h_bytes = p->d2h;
+  prof_reset(p);
   return SIGW_OK;
 }
 

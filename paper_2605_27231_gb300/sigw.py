@@ -37,6 +37,16 @@ class NGMap(C.Structure):
     _fields_ = [("kind", C.c_int), ("F_NL", C.c_double), ("G_NL", C.c_double), ("usr_floor", C.c_double)]
 
 
+NKINDS = 7
+KINDS = ("synth", "p1_inv_axis0_filter", "p2_inv_axis1", "p3_inv_axis2_product_fwd_axis2", "f2_fwd_axis1",
+         "f3_fwd_axis0_tt_bin", "bin_finalise")
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * NKINDS), ("bytes", C.c_double * NKINDS), ("launches", C.c_int64 * NKINDS),
+                ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double)]
+
+
 _lib = None
 _dbl = C.POINTER(C.c_double)
 _i64 = C.POINTER(C.c_int64)
@@ -68,6 +78,8 @@ def lib():
         "sigw_decompose": (C.c_int, [C.POINTER(Opts), C.c_int, _dbl, _dbl, _dbl, _dbl]),
         "sigw_cell_table": (C.c_int, [C.POINTER(Opts), C.c_int, C.c_int, C.POINTER(C.c_int16)]),
         "sigw_debug_fail_alloc": (C.c_int, [C.c_int]),
+        "sigw_plan_profile": (C.c_int, [P, C.c_int]),
+        "sigw_plan_profile_read": (C.c_int, [P, C.POINTER(Profile)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -218,6 +230,18 @@ class Plan:
 
     def fft3d(self, direction, in_ptr, out_ptr):
         _check(lib().sigw_fft3d(self._h, direction, C.c_void_p(in_ptr), C.c_void_p(out_ptr)), self._h, "sigw_fft3d")
+
+    def profile(self, enable=True):
+        _check(lib().sigw_plan_profile(self._h, 1 if enable else 0), self._h, "sigw_plan_profile")
+
+    def profile_read(self):
+        """Counters since the last reset: dict kind -> {ms, bytes, launches}, plus h2d/d2h bytes."""
+        pr = Profile()
+        _check(lib().sigw_plan_profile_read(self._h, C.byref(pr)), self._h, "sigw_plan_profile_read")
+        out = {k: {"ms": pr.ms[i], "bytes": pr.bytes[i], "launches": int(pr.launches[i])} for i, k in enumerate(KINDS)}
+        out["h2d_bytes"] = pr.h2d_bytes
+        out["d2h_bytes"] = pr.d2h_bytes
+        return out
 
     def synchronize(self):
         _check(lib().sigw_synchronize(self._h), self._h, "sigw_synchronize")
