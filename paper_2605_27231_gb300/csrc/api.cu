@@ -112,6 +112,7 @@ struct sigw_plan_s {
   double* d_mean = nullptr;
   unsigned long long* d_hits = nullptr;
   uint64_t* d_seeds = nullptr;
+  int* d_err = nullptr;  // OR-ed by kernels whose bounded waits gave up
   int generated = 0;
   std::string err;
   // accounting (see sigw_profile)
@@ -205,6 +206,18 @@ sigw_status run(sigw_plan p, int kind, double bytes, const char* what, F&& f) {
     sigw_status _s = run(plan, kind, (double)(bytes), what, [&]() { return (expr); }); \
     if (_s != SIGW_OK) return _s;                                                 \
   } while (0)
+
+// After the stream is idle: report (and clear) a bounded wait that gave up inside a kernel.
+sigw_status check_err_flag(sigw_plan p) {
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(p, e, "read error flag");
+  if (h) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return fail(p, SIGW_ETIMEOUT, "a bounded wait in the bulk-copy pipeline gave up; results are invalid");
+  }
+  return SIGW_OK;
+}
 
 sigw_status dev_alloc(sigw_plan p, void** ptr, size_t bytes) {
   int c = g_fail_alloc.load();
@@ -403,7 +416,9 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
   ALLOC(p->d_mean, mb * sizeof(double));
   ALLOC(p->d_hits, mb * sizeof(unsigned long long));
   ALLOC(p->d_seeds, mb * sizeof(uint64_t));
+  ALLOC(p->d_err, sizeof(int));
 #undef ALLOC
+  if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return bail(SIGW_ECUDA);
   // tables
   std::vector<unsigned char> buf;
   {
@@ -461,7 +476,7 @@ sigw_status sigw_synchronize(sigw_plan p) {
   if (!p) return SIGW_EINVAL;
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
   CKP(p, cudaStreamSynchronize(p->st), "stream synchronize");
-  return SIGW_OK;
+  return check_err_flag(p);
 }
 
 sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* map, const uint64_t* seeds, int batch,
@@ -584,7 +599,7 @@ sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, do
         RUN(p, 2, 5.0 * nb * fieldb, "P2", OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, st));
       }
       RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
-          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, st));
+          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, st));
       RUN(p, 4, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
           OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st));
       RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3",
@@ -610,6 +625,10 @@ sigw_status sigw_spectrum(sigw_plan p, const int* shells, int n_shells, double* 
       "download results");
   p->d2h += host.size() * sizeof(double);
   CKP(p, cudaStreamSynchronize(p->st), "spectrum");
+  {
+    sigw_status fs = check_err_flag(p);
+    if (fs != SIGW_OK) return fs;
+  }
   for (int i = 0; i < batch * ns; ++i) {
     if (PA) PA[i] = host[4 * i + 0];
     if (PB) PB[i] = host[4 * i + 1];

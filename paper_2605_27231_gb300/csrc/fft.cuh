@@ -125,11 +125,41 @@ template <int N, int E> struct StockPlan {
   static_assert(RLAST >= 2 && RLAST <= E, "bad factorisation");
 };
 
-// Shared-memory footprint of one pencil's exchange buffers: two ping-pong buffers,
-// each with separate re / im arrays of pencil_buf_elems<N>() elements of T.
-template <int N> __host__ __device__ constexpr int pencil_buf_elems() { return N + N / 32 + 1; }
-template <int N> __host__ __device__ constexpr int pencil_smem_elems() { return 4 * pencil_buf_elems<N>(); }
-__device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
+// ---------------------------------------------------------------- exchange layouts
+// Exchange buffers hold complex values (one 64-bit (FP32) or 128-bit (FP64) access per element) in two
+// ping-pong buffers, so a stage reads one buffer and writes the other with one barrier per stage.
+//
+// RowLayout: one pencil per group of P consecutive threads, private buffer, element p at p + p/16.
+//   Stage-0 writes (stride E between threads) and unit-stride reads then fall in distinct banks.
+// ColLayout<TC, E>: TC adjacent pencils (thread = j * TC + c) interleaved as [p][c]; rows are permuted
+//   within aligned groups of G = (128 B / element) / TC positions by g(p) = (p + p/E) mod G, so the G
+//   positions touched by one access phase of a warp (stride 1 or stride E) land on distinct banks.
+template <typename T, int N> struct RowLayout {
+  static constexpr int BUF = N + N / 16 + 1;  // elements per buffer
+  static constexpr int SIZE = 2 * BUF;        // elements per pencil (both buffers)
+  cx<T>* base;
+  __device__ __forceinline__ cx<T>* buf(int which) const { return base + which * BUF; }
+  __device__ __forceinline__ int idx(int p) const { return p + (p >> 4); }
+};
+
+template <typename T, int N, int TC, int E> struct ColLayout {
+  static constexpr int PER_PHASE = 128 / (int)sizeof(cx<T>);
+  static constexpr int G0 = PER_PHASE / TC;
+  static constexpr int G = G0 < 1 ? 1 : G0;
+  static constexpr int BUF = N * TC;
+  static constexpr int SIZE = 2 * BUF;  // elements for all TC pencils (both buffers)
+  cx<T>* base;  // shared by the TC pencils of the CTA
+  int c;
+  __device__ __forceinline__ cx<T>* buf(int which) const { return base + which * BUF; }
+  __device__ __forceinline__ int idx(int p) const {
+    if constexpr (G == 1) {
+      return p * TC + c;
+    } else {
+      const int q = (p & ~(G - 1)) + ((p + p / E) & (G - 1));
+      return q * TC + c;
+    }
+  }
+};
 
 struct SyncBlock { __device__ __forceinline__ void operator()() const { __syncthreads(); } };
 struct SyncWarp { __device__ __forceinline__ void operator()() const { __syncwarp(); } };
@@ -140,48 +170,31 @@ __device__ __forceinline__ cx<T> twiddle(const cx<T>* __restrict__ tw, int idx) 
   cx<T> w = __ldg(tw + idx);
   return DIR > 0 ? conjg<T>(w) : w;
 }
-template <> __device__ __forceinline__ cx<double> twiddle<double, 1>(const cx<double>* __restrict__ tw, int idx) {
-  cx<double> w = tw[idx];
-  return conjg<double>(w);
-}
-template <> __device__ __forceinline__ cx<double> twiddle<double, -1>(const cx<double>* __restrict__ tw, int idx) {
-  return tw[idx];
-}
 
 // Stage s >= 1 of the Stockham recursion: reads buffer (s-1)&1, writes buffer s&1.
-template <typename T, int N, int E, int DIR, int s, typename Sync>
-__device__ __forceinline__ void stock_stage(cx<T> (&v)[E], int j, T* __restrict__ sm, const cx<T>* __restrict__ tw,
+template <typename T, int N, int E, int DIR, int s, typename Lay, typename Sync>
+__device__ __forceinline__ void stock_stage(cx<T> (&v)[E], int j, const Lay& L, const cx<T>* __restrict__ tw,
                                             Sync sync) {
   using PL = StockPlan<N, E>;
   constexpr int P = PL::P;
   constexpr int S = PL::S;
-  constexpr int B = pencil_buf_elems<N>();
   constexpr int Ns = ipow(E, s);
-  const T* rre = sm + ((s - 1) & 1) * 2 * B;
-  const T* rim = rre + B;
+  const cx<T>* rd = L.buf((s - 1) & 1);
   if constexpr (s < S - 1) {
-    T* wre = sm + (s & 1) * 2 * B;
-    T* wim = wre + B;
+    cx<T>* wr = L.buf(s & 1);
     const int jj = j;
     const int k = jj & (Ns - 1);
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int p = padx(jj + r * P);
-      v[r] = mk<T>(rre[p], rim[p]);
-    }
+    for (int r = 0; r < E; ++r) v[r] = rd[L.idx(jj + r * P)];
     constexpr int stride = N / (Ns * E);
 #pragma unroll
     for (int r = 1; r < E; ++r) v[r] = mul<T>(v[r], twiddle<T, DIR>(tw, r * k * stride));
     dftR<T, DIR, E>(v);
     const int base = (jj / Ns) * Ns * E + k;
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int p = padx(base + r * Ns);
-      wre[p] = v[r].x;
-      wim[p] = v[r].y;
-    }
+    for (int r = 0; r < E; ++r) wr[L.idx(base + r * Ns)] = v[r];
     sync();
-    stock_stage<T, N, E, DIR, s + 1, Sync>(v, j, sm, tw, sync);
+    stock_stage<T, N, E, DIR, s + 1, Lay, Sync>(v, j, L, tw, sync);
   } else {
     constexpr int R = PL::RLAST;
     constexpr int NB = E / R;
@@ -191,10 +204,7 @@ __device__ __forceinline__ void stock_stage(cx<T> (&v)[E], int j, T* __restrict_
       const int k = jj & (Ns - 1);
       cx<T> a[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int p = padx(jj + r * (N / R));
-        a[r] = mk<T>(rre[p], rim[p]);
-      }
+      for (int r = 0; r < R; ++r) a[r] = rd[L.idx(jj + r * (N / R))];
       constexpr int stride = N / (Ns * R);
 #pragma unroll
       for (int r = 1; r < R; ++r) a[r] = mul<T>(a[r], twiddle<T, DIR>(tw, r * k * stride));
@@ -205,29 +215,23 @@ __device__ __forceinline__ void stock_stage(cx<T> (&v)[E], int j, T* __restrict_
   }
 }
 
-// Full pencil transform (see the file header for the data convention).  `sm` points to this
-// pencil's pencil_smem_elems<N>() elements.  Every thread of the synchronisation group must call
-// it (no divergent early exit).  With TRAIL, a final barrier lets the caller reuse `sm` at once.
-template <typename T, int N, int E, int DIR, typename Sync, bool TRAIL = true>
-__device__ __forceinline__ void fft_pencil(cx<T> (&v)[E], int j, T* __restrict__ sm, const cx<T>* __restrict__ tw,
+// Full pencil transform (see the file header for the data convention).  Every thread of the
+// synchronisation group must call it (no divergent early exit).  With TRAIL, a final barrier lets
+// the caller reuse the exchange buffers at once.
+template <typename T, int N, int E, int DIR, typename Lay, typename Sync, bool TRAIL = true>
+__device__ __forceinline__ void fft_pencil(cx<T> (&v)[E], int j, const Lay& L, const cx<T>* __restrict__ tw,
                                            Sync sync) {
   using PL = StockPlan<N, E>;
   if constexpr (PL::S == 1) {
     dftR<T, DIR, E>(v);
   } else {
-    constexpr int B = pencil_buf_elems<N>();
-    T* wre = sm;
-    T* wim = sm + B;
+    cx<T>* wr = L.buf(0);
     dftR<T, DIR, E>(v);
     const int base = j * E;  // Ns = 1
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int p = padx(base + r);
-      wre[p] = v[r].x;
-      wim[p] = v[r].y;
-    }
+    for (int r = 0; r < E; ++r) wr[L.idx(base + r)] = v[r];
     sync();
-    stock_stage<T, N, E, DIR, 1, Sync>(v, j, sm, tw, sync);
+    stock_stage<T, N, E, DIR, 1, Lay, Sync>(v, j, L, tw, sync);
     if constexpr (TRAIL) sync();
   }
 }

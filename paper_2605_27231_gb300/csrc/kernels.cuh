@@ -91,10 +91,10 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>
   using SH = Shape<T, N>;
   constexpr int E = SH::ER, P = SH::PR, H = N / 2;
   constexpr int PPC = SH::RPC;  // row pairs per CTA
-  constexpr int B = pencil_buf_elems<N>();
   using Sync = typename RowSync<P>::type;
-  extern __shared__ unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw) + (threadIdx.x / P) * pencil_smem_elems<N>();
+  using Lay = RowLayout<T, N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Lay L{reinterpret_cast<cx<T>*>(smraw) + (threadIdx.x / P) * Lay::SIZE};
   const int j = threadIdx.x % P;
   const int b = blockIdx.y;
   const long pair = (long)blockIdx.x * PPC + threadIdx.x / P;
@@ -145,15 +145,10 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>
     for (int o = 16; o > 0; o >>= 1) myhits += __shfl_down_sync(0xffffffffu, myhits, o);
     if ((threadIdx.x & 31) == 0 && myhits) atomicAdd(hits + b, myhits);
   }
-  fft_pencil<T, N, E, -1, Sync>(v, j, sm, tw, Sync());
-  T* zre = sm;
-  T* zim = sm + B;
+  fft_pencil<T, N, E, -1, Lay, Sync>(v, j, L, tw, Sync());
+  cx<T>* zb = L.buf(0);
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int p = padx(j + r * P);
-    zre[p] = v[r].x;
-    zim[p] = v[r].y;
-  }
+  for (int r = 0; r < E; ++r) zb[L.idx(j + r * P)] = v[r];
   Sync()();
   if (live) {
     cx<T>* y1 = Y + ((long)b * N * N + row0) * H;
@@ -162,15 +157,13 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>
     for (int r = 0; r < E / 2; ++r) {
       const int c = j + r * P;
       if (c == 0) {
-        const cx<T> z0 = mk<T>(zre[0], zim[0]);
-        const int ph = padx(H);
-        const cx<T> zh = mk<T>(zre[ph], zim[ph]);
+        const cx<T> z0 = zb[L.idx(0)];
+        const cx<T> zh = zb[L.idx(H)];
         y1[0] = mk<T>(z0.x, zh.x);
         y2[0] = mk<T>(z0.y, zh.y);
       } else {
-        const int pc = padx(c), pm = padx(N - c);
-        const cx<T> zc = mk<T>(zre[pc], zim[pc]);
-        const cx<T> zm = mk<T>(zre[pm], -zim[pm]);  // conj Z(N-c)
+        const cx<T> zc = zb[L.idx(c)];
+        const cx<T> zm = conjg<T>(zb[L.idx(N - c)]);
         y1[c] = mk<T>((T)0.5 * (zc.x + zm.x), (T)0.5 * (zc.y + zm.y));
         y2[c] = mk<T>((T)0.5 * (zc.y - zm.y), (T)-0.5 * (zc.x - zm.x));
       }
@@ -187,8 +180,9 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const cx<T>* __restrict__ Y, T
   constexpr int E = SH::ER, P = SH::PR, H = N / 2;
   constexpr int PPC = SH::RPC;
   using Sync = typename RowSync<P>::type;
-  extern __shared__ unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw) + (threadIdx.x / P) * pencil_smem_elems<N>();
+  using Lay = RowLayout<T, N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Lay L{reinterpret_cast<cx<T>*>(smraw) + (threadIdx.x / P) * Lay::SIZE};
   __shared__ double red[32];
   const int j = threadIdx.x % P;
   const int b = blockIdx.y;
@@ -219,7 +213,7 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const cx<T>* __restrict__ Y, T
     }
     v[r] = mk<T>(a.x - c.y, a.y + c.x);  // a + i c
   }
-  fft_pencil<T, N, E, +1, Sync>(v, j, sm, tw, Sync());
+  fft_pencil<T, N, E, +1, Lay, Sync>(v, j, L, tw, Sync());
   double sq = 0.0;
   if (live) {
     T* r1 = R + ((long)b * N * N + row0) * N;
@@ -249,9 +243,10 @@ template <typename T, int N, int DIR, int AX>
 __global__ void __launch_bounds__(256) k_pass(cx<T>* __restrict__ Y, const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
-  extern __shared__ unsigned char smraw[];
+  using Lay = ColLayout<T, N, TC, E>;
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
-  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int col = blockIdx.x * TC + c;
   const int o = blockIdx.y;
   const int b = blockIdx.z;
@@ -261,7 +256,7 @@ __global__ void __launch_bounds__(256) k_pass(cx<T>* __restrict__ Y, const cx<T>
   cx<T> v[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) v[r] = base[(j + r * P) * stride];
-  fft_pencil<T, N, E, DIR, SyncBlock, false>(v, j, sm, tw, SyncBlock());
+  fft_pencil<T, N, E, DIR, Lay, SyncBlock, false>(v, j, L, tw, SyncBlock());
 #pragma unroll
   for (int r = 0; r < E; ++r) base[(j + r * P) * stride] = v[r];
 }
@@ -341,13 +336,13 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
                                             const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2, NH = H + 1;
-  extern __shared__ unsigned char smraw[];
-  T* sm_pen = reinterpret_cast<T*>(smraw);
-  T* sm_tab = sm_pen + TC * pencil_smem_elems<N>();   // nb * nm1
-  cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(sm_tab + ((nb * nm1 + 1) & ~1));  // N values (column 0 only)
-  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);                              // N cells
+  using Lay = ColLayout<T, N, TC, E>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(smraw) + Lay::SIZE;  // N values (column 0 only)
+  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);              // N cells
+  T* sm_tab = reinterpret_cast<T*>(sm_cn + N);                  // nb * nm1
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
-  T* sm = sm_pen + c * pencil_smem_elems<N>();
+  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int cc = blockIdx.x * TC + c;
   const int k1 = blockIdx.y;
   const int b = blockIdx.z;
@@ -392,11 +387,11 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
       const T nd = (T)derivn(j + r * P, N);
       w[r] = mk<T>(-nd * v[r].y, nd * v[r].x);  // i n0 v
     }
-    fft_pencil<T, N, E, +1, SyncBlock>(v, j, sm, tw, SyncBlock());
+    fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
     cx<T>* ta = Ta + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
 #pragma unroll
     for (int r = 0; r < E; ++r) ta[(long)(j + r * P) * N * H] = v[r];
-    fft_pencil<T, N, E, +1, SyncBlock>(w, j, sm, tw, SyncBlock());
+    fft_pencil<T, N, E, +1, Lay, SyncBlock>(w, j, L, tw, SyncBlock());
     cx<T>* tb = Tb + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
 #pragma unroll
     for (int r = 0; r < E; ++r) tb[(long)(j + r * P) * N * H] = w[r];
@@ -413,9 +408,10 @@ __global__ void __launch_bounds__(256) k_p2(const cx<T>* __restrict__ Ta, const 
                                             const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
-  extern __shared__ unsigned char smraw[];
+  using Lay = ColLayout<T, N, TC, E>;
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
-  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int cc = blockIdx.x * TC + c;
   const int a0 = blockIdx.y;
   const int b = blockIdx.z / nb, a = blockIdx.z % nb;
@@ -431,96 +427,181 @@ __global__ void __launch_bounds__(256) k_p2(const cx<T>* __restrict__ Ta, const 
     w[r] = mk<T>(-nd * v[r].y, nd * v[r].x);
   }
   auto wout = [&](int f) { return W + (((long)b * 3 + f) * n_alpha + alpha0 + a) * fstride + off; };
-  fft_pencil<T, N, E, +1, SyncBlock>(v, j, sm, tw, SyncBlock());
+  fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
   cx<T>* o0 = wout(0);
 #pragma unroll
   for (int r = 0; r < E; ++r) o0[(long)(j + r * P) * H] = v[r];
-  fft_pencil<T, N, E, +1, SyncBlock>(w, j, sm, tw, SyncBlock());
+  fft_pencil<T, N, E, +1, Lay, SyncBlock>(w, j, L, tw, SyncBlock());
   cx<T>* o1 = wout(1);
 #pragma unroll
   for (int r = 0; r < E; ++r) o1[(long)(j + r * P) * H] = w[r];
 #pragma unroll
   for (int r = 0; r < E; ++r) v[r] = tb[(long)(j + r * P) * H];
-  fft_pencil<T, N, E, +1, SyncBlock, false>(v, j, sm, tw, SyncBlock());
+  fft_pencil<T, N, E, +1, Lay, SyncBlock, false>(v, j, L, tw, SyncBlock());
   cx<T>* o2 = wout(2);
 #pragma unroll
   for (int r = 0; r < E; ++r) o2[(long)(j + r * P) * H] = v[r];
 }
 
-// 1-D Hermitian spectrum value at index k (0..N-1) of a packed row:
+// ---------------------------------------------------------------- bulk-copy pipeline helpers
+// cp.async.bulk (TMA, 1-D) global -> shared with mbarrier completion.  Waits are bounded: after about a
+// second of spinning the wait sets *err and gives up, so a lost copy can never hang the GPU.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+}
+
+template <typename T, int N> struct P3Cfg {
+  static constexpr int H = N / 2;
+  static constexpr int E = (N >= 16) ? 8 : 4;
+  static constexpr int P = N / E;
+  static constexpr int RPC0 = 8192 / (H * (int)sizeof(cx<T>));  // one 8 KB bulk copy per (field, term)
+  static constexpr int RPC = RPC0 > N * N ? N * N : RPC0;
+  static constexpr int THREADS = RPC * P;
+  static constexpr int STAGES = 3;
+  static constexpr int STAGE_ELEMS = 6 * RPC * H;  // three fields of two terms
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_ELEMS * sizeof(cx<T>) +
+                                 (size_t)RPC * RowLayout<T, N>::SIZE * sizeof(cx<T>) + STAGES * sizeof(uint64_t);
+};
+
+// 1-D Hermitian spectrum value at index k (0..N-1) of a packed row held in shared memory:
 //   plain: k = 0 -> Re row[0], k = H -> Im row[0], else row[k] or conj(row[N-k]);
 //   grad : i n^D(k) times the plain value, zero at k = 0 and k = H (the packed column is not read).
 template <typename T, int N>
-__device__ __forceinline__ cx<T> herm_plain(const cx<T>* __restrict__ row, int k) {
+__device__ __forceinline__ cx<T> herm_plain(const cx<T>* row, int k) {
   constexpr int H = N / 2;
-  if (k == 0) return mk<T>(__ldg(&row[0].x), (T)0);
-  if (k == H) return mk<T>(__ldg(&row[0].y), (T)0);
-  if (k < H) return __ldg(row + k);
-  return conjg<T>(__ldg(row + (N - k)));
+  if (k == 0) return mk<T>(row[0].x, (T)0);
+  if (k == H) return mk<T>(row[0].y, (T)0);
+  if (k < H) return row[k];
+  return conjg<T>(row[N - k]);
 }
 template <typename T, int N>
-__device__ __forceinline__ cx<T> herm_grad(const cx<T>* __restrict__ row, int k) {
+__device__ __forceinline__ cx<T> herm_grad(const cx<T>* row, int k) {
   constexpr int H = N / 2;
   if (k == 0 || k == H) return mk<T>((T)0, (T)0);
   cx<T> x;
   T n;
   if (k < H) {
-    x = __ldg(row + k);
+    x = row[k];
     n = (T)k;
   } else {
-    x = conjg<T>(__ldg(row + (N - k)));
+    x = conjg<T>(row[N - k]);
     n = (T)(k - N);
   }
   return mk<T>(-n * x.y, n * x.x);
 }
 
-// P3: last inverse pass (axis 2, C2R) of all terms for RPC rows, the product
-//   s_ij(x) = sum_a sigma_a g^a_i(x) g^a_j(x)  (six components, FP32/FP64 registers),
+// P3: last inverse pass (axis 2, C2R) of all terms for RPC consecutive rows, the product
+//   s_ij(x) = sum_a sigma_a g^a_i(x) g^a_j(x)  (six components in registers),
 // then the forward R2C of s_ij along axis 2 keeping k2 = 0..n_c, written to F[b][comp][a0][a1][k2].
 // Term pair (a, a+1) uses three complex transforms: (g2^a + i g1^a), (g0^a + i g0^{a+1}), (g2^{a+1} + i g1^{a+1}).
+// The six packed rows of a term pair stream into a STAGES-deep shared-memory ring by cp.async.bulk,
+// issued STAGES-1 pairs ahead by thread 0.
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_p3(const cx<T>* __restrict__ W, const T* __restrict__ sigma, int n_alpha,
-                                            cx<T>* __restrict__ F, int n_c, const cx<T>* __restrict__ tw) {
-  using SH = Shape<T, N>;
-  constexpr int E = SH::ER, P = SH::PR, H = N / 2, RPC = SH::RPC;
-  constexpr int B = pencil_buf_elems<N>();
+__global__ void __launch_bounds__(P3Cfg<T, N>::THREADS) k_p3(const cx<T>* __restrict__ W, const T* __restrict__ sigma,
+                                                             int n_alpha, cx<T>* __restrict__ F, int n_c,
+                                                             const cx<T>* __restrict__ tw, int* __restrict__ err) {
+  using CF = P3Cfg<T, N>;
+  constexpr int E = CF::E, P = CF::P, H = N / 2, RPC = CF::RPC, STAGES = CF::STAGES;
   using Sync = typename RowSync<P>::type;
-  extern __shared__ unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw) + (threadIdx.x / P) * pencil_smem_elems<N>();
-  const int j = threadIdx.x % P;
-  const long row = (long)blockIdx.x * RPC + threadIdx.x / P;  // a0 * N + a1 (always < N*N: RPC divides N*N)
+  using Lay = RowLayout<T, N>;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  cx<T>* ring = reinterpret_cast<cx<T>*>(smraw);
+  cx<T>* xch = ring + STAGES * CF::STAGE_ELEMS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xch + RPC * Lay::SIZE);
+  const int rr = threadIdx.x / P, j = threadIdx.x % P;
+  const Lay L{xch + rr * Lay::SIZE};
+  const long row0 = (long)blockIdx.x * RPC;
+  const long row = row0 + rr;
   const int b = blockIdx.y;
   const long fstride = (long)N * N * H;
-  auto wrow = [&](int f, int a) { return W + (((long)b * 3 + f) * n_alpha + a) * fstride + row * H; };
+  const int npairs = (n_alpha + 1) / 2;
+  constexpr uint32_t COPY = RPC * H * sizeof(cx<T>);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(bars + s, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int pr) {  // thread 0: the six rows blocks of term pair pr into stage pr % STAGES
+    const int s = pr % STAGES, a = 2 * pr;
+    const bool two = a + 1 < n_alpha;
+    cx<T>* dst = ring + s * CF::STAGE_ELEMS;
+    fence_proxy_async();
+    mbar_expect_tx(bars + s, (two ? 6u : 3u) * COPY);
+    for (int f = 0; f < 3; ++f) {
+      bulk_g2s(dst + f * RPC * H, W + (((long)b * 3 + f) * n_alpha + a) * fstride + row0 * H, COPY, bars + s);
+      if (two) bulk_g2s(dst + (3 + f) * RPC * H, W + (((long)b * 3 + f) * n_alpha + a + 1) * fstride + row0 * H, COPY,
+                        bars + s);
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int pr = 0; pr < STAGES - 1 && pr < npairs; ++pr) issue(pr);
   T acc[6][E];
 #pragma unroll
   for (int q = 0; q < 6; ++q)
 #pragma unroll
     for (int r = 0; r < E; ++r) acc[q][r] = (T)0;
-  for (int a = 0; a < n_alpha; a += 2) {
-    const bool two = (a + 1) < n_alpha;
-    const cx<T>* wb0 = wrow(0, a);
-    const cx<T>* w10 = wrow(1, a);
-    const cx<T>* w20 = wrow(2, a);
-    const cx<T>* wb1 = wrow(0, two ? a + 1 : a);
-    const cx<T>* w11 = wrow(1, two ? a + 1 : a);
-    const cx<T>* w21 = wrow(2, two ? a + 1 : a);
+  bool ok = true;
+  for (int pr = 0; pr < npairs; ++pr) {
+    const int s = pr % STAGES;
+    if (threadIdx.x == 0 && pr + STAGES - 1 < npairs) issue(pr + STAGES - 1);
+    if (ok) ok = mbar_wait(bars + s, (uint32_t)((pr / STAGES) & 1), err);
+    const int a = 2 * pr;
+    const bool two = a + 1 < n_alpha;
+    const cx<T>* st = ring + s * CF::STAGE_ELEMS + rr * H;
+    const cx<T>* wb0 = st;
+    const cx<T>* w10 = st + RPC * H;
+    const cx<T>* w20 = st + 2 * RPC * H;
+    const cx<T>* wb1 = st + 3 * RPC * H;
+    const cx<T>* w11 = st + 4 * RPC * H;
+    const cx<T>* w21 = st + 5 * RPC * H;
     cx<T> zA[E], zB[E], zC[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int k = j + r * P;
       const cx<T> g2 = herm_grad<T, N>(wb0, k), g1 = herm_plain<T, N>(w10, k);
       const cx<T> g0 = herm_plain<T, N>(w20, k);
-      cx<T> g0b = herm_plain<T, N>(w21, k);
-      if (!two) g0b = mk<T>((T)0, (T)0);
-      const cx<T> h2 = herm_grad<T, N>(wb1, k), h1 = herm_plain<T, N>(w11, k);
+      cx<T> g0b = mk<T>((T)0, (T)0), h2 = g0b, h1 = g0b;
+      if (two) {
+        g0b = herm_plain<T, N>(w21, k);
+        h2 = herm_grad<T, N>(wb1, k);
+        h1 = herm_plain<T, N>(w11, k);
+      }
       zA[r] = mk<T>(g2.x - g1.y, g2.y + g1.x);
       zB[r] = mk<T>(g0.x - g0b.y, g0.y + g0b.x);
       zC[r] = mk<T>(h2.x - h1.y, h2.y + h1.x);
     }
-    fft_pencil<T, N, E, +1, Sync>(zA, j, sm, tw, Sync());
-    fft_pencil<T, N, E, +1, Sync>(zB, j, sm, tw, Sync());
-    fft_pencil<T, N, E, +1, Sync>(zC, j, sm, tw, Sync());
+    fft_pencil<T, N, E, +1, Lay, Sync>(zA, j, L, tw, Sync());
+    fft_pencil<T, N, E, +1, Lay, Sync>(zB, j, L, tw, Sync());
+    fft_pencil<T, N, E, +1, Lay, Sync>(zC, j, L, tw, Sync());
     const T sa = sigma[a];
     const T sb = two ? sigma[a + 1] : (T)0;
 #pragma unroll
@@ -546,31 +627,27 @@ __global__ void __launch_bounds__(256) k_p3(const cx<T>* __restrict__ W, const T
         acc[5][r] += s1 * g2;
       }
     }
+    __syncthreads();  // stage s fully read before it is refilled
   }
   // forward R2C of the six real rows, two per complex transform
-  T* zre = sm;
-  T* zim = sm + B;
+  cx<T>* zb = L.buf(0);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     cx<T> z[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) z[r] = mk<T>(acc[2 * q][r], acc[2 * q + 1][r]);
-    fft_pencil<T, N, E, -1, Sync>(z, j, sm, tw, Sync());
+    fft_pencil<T, N, E, -1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int p = padx(j + r * P);
-      zre[p] = z[r].x;
-      zim[p] = z[r].y;
-    }
+    for (int r = 0; r < E; ++r) zb[L.idx(j + r * P)] = z[r];
     Sync()();
     const int ncp = n_c + 1;
     cx<T>* f1 = F + (((long)b * 6 + 2 * q) * N * N + row) * ncp;
     cx<T>* f2 = F + (((long)b * 6 + 2 * q + 1) * N * N + row) * ncp;
     for (int k = j; k <= n_c; k += P) {
-      const int pk = padx(k), pm = padx((N - k) & (N - 1));
-      const T zr = zre[pk], zi = zim[pk], mr = zre[pm], mi = -zim[pm];
-      f1[k] = mk<T>((T)0.5 * (zr + mr), (T)0.5 * (zi + mi));
-      f2[k] = mk<T>((T)0.5 * (zi - mi), (T)-0.5 * (zr - mr));
+      const cx<T> zk = zb[L.idx(k)];
+      const cx<T> zm = conjg<T>(zb[L.idx((N - k) & (N - 1))]);
+      f1[k] = mk<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y + zm.y));
+      f2[k] = mk<T>((T)0.5 * (zk.y - zm.y), (T)-0.5 * (zk.x - zm.x));
     }
     Sync()();
   }
@@ -582,9 +659,10 @@ __global__ void __launch_bounds__(256) k_f2(const cx<T>* __restrict__ F, cx<T>* 
                                             int nk1, const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ES, P = SH::PS, TC = SH::TC;
-  extern __shared__ unsigned char smraw[];
+  using Lay = ColLayout<T, N, TC, E>;
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
-  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int ncp = n_c + 1;
   const int cc = blockIdx.x * TC + c;
   const bool valid = cc < ncp;
@@ -594,7 +672,7 @@ __global__ void __launch_bounds__(256) k_f2(const cx<T>* __restrict__ F, cx<T>* 
   cx<T> v[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) v[r] = valid ? in[(long)(j + r * P) * ncp] : mk<T>((T)0, (T)0);
-  fft_pencil<T, N, E, -1, SyncBlock, false>(v, j, sm, tw, SyncBlock());
+  fft_pencil<T, N, E, -1, Lay, SyncBlock, false>(v, j, L, tw, SyncBlock());
   if (valid) {
     cx<T>* out = F2 + (bc * N + a0) * (long)nk1 * ncp + cc;
 #pragma unroll
@@ -648,10 +726,11 @@ __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_
                                             const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::E3, P = SH::P3, TC = SH::TC3, H = N / 2;
-  extern __shared__ unsigned char smraw[];
+  using Lay = ColLayout<T, N, TC, E>;
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
-  T* sm = reinterpret_cast<T*>(smraw) + c * pencil_smem_elems<N>();
+  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int ncp = n_c + 1;
   const int k1i = blockIdx.y;
   const int n1 = n1lo + k1i;
@@ -672,7 +751,7 @@ __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_
     const cx<T>* in = F2 + (((long)b * 6 + q) * N * nk1 + k1i) * (long)ncp + (valid ? cc : 0);
 #pragma unroll
     for (int r = 0; r < E; ++r) X[q][r] = valid ? in[(long)(j + r * P) * nk1 * ncp] : mk<T>((T)0, (T)0);
-    fft_pencil<T, N, E, -1, SyncBlock>(X[q], j, sm, tw, SyncBlock());
+    fft_pencil<T, N, E, -1, Lay, SyncBlock>(X[q], j, L, tw, SyncBlock());
   }
   double acc = 0.0;
   if (valid) {

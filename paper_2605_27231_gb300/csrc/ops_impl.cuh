@@ -22,14 +22,16 @@ struct OpsT {
   using C = cx<T>;
 
   template <int N>
-  static size_t pen_bytes(int count) { return (size_t)count * pencil_smem_elems<N>() * sizeof(T); }
+  static size_t row_bytes(int count) { return (size_t)count * RowLayout<T, N>::SIZE * sizeof(C); }
+  template <int N, int TC, int E>
+  static size_t col_bytes() { return (size_t)ColLayout<T, N, TC, E>::SIZE * sizeof(C); }
 
   // ------------------------------------------------------------ synthesis
   template <int N, int MODE>
   static cudaError_t rows_r2c_n(const void* R, void* Y, const uint64_t* seeds, MapArgs map, const double* mean,
                                 unsigned long long* hits, int batch, const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::RPC);
+    const size_t sm = row_bytes<N>(SH::RPC);
     auto k = k_rows_r2c<T, N, MODE>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     dim3 grid((N * N / 2) / SH::RPC, batch);
@@ -40,7 +42,7 @@ struct OpsT {
   static cudaError_t rows_c2r_n(const void* Y, void* R, int batch, double scale, double* sqp, const void* tw,
                                 cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::RPC);
+    const size_t sm = row_bytes<N>(SH::RPC);
     auto k = k_rows_c2r<T, N, SQ>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     dim3 grid((N * N / 2) / SH::RPC, batch);
@@ -50,7 +52,7 @@ struct OpsT {
   template <int N, int DIR, int AX>
   static cudaError_t pass_n(void* Y, int batch, const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::TC);
+    const size_t sm = col_bytes<N, SH::TC, SH::ES>();
     auto k = k_pass<T, N, DIR, AX>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     dim3 grid((N / 2) / SH::TC, N, batch);
@@ -62,7 +64,7 @@ struct OpsT {
   static cudaError_t p1_n(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
                           int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::TC) + (size_t)((nb * nm1 + 1) & ~1) * sizeof(T) + N * sizeof(C) + N * sizeof(int);
+    const size_t sm = col_bytes<N, SH::TC, SH::ES>() + N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
     auto k = k_p1<T, N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
     dim3 grid((N / 2) / SH::TC, N, batch);
@@ -74,7 +76,7 @@ struct OpsT {
   static cudaError_t p2_n(const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
                           const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::TC);
+    const size_t sm = col_bytes<N, SH::TC, SH::ES>();
     auto k = k_p2<T, N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     dim3 grid((N / 2) / SH::TC, N, batch * nb);
@@ -83,13 +85,12 @@ struct OpsT {
   }
   template <int N>
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
-                          cudaStream_t st) {
-    using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::RPC);
+                          int* err, cudaStream_t st) {
+    using CF = P3Cfg<T, N>;
     auto k = k_p3<T, N>;
-    SIGW_CHECK_LAUNCH(allow_smem(k, sm));
-    dim3 grid((N * N) / SH::RPC, batch);
-    k<<<grid, SH::RPC * SH::PR, sm, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw);
+    SIGW_CHECK_LAUNCH(allow_smem(k, CF::SMEM));
+    dim3 grid((N * N) / CF::RPC, batch);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw, err);
     return cudaGetLastError();
   }
   static void n1_range(int N, int n_c, int* lo, int* nk1) {
@@ -102,7 +103,7 @@ struct OpsT {
   template <int N>
   static cudaError_t f2_n(const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::TC);
+    const size_t sm = col_bytes<N, SH::TC, SH::ES>();
     auto k = k_f2<T, N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     int lo, nk1;
@@ -115,7 +116,7 @@ struct OpsT {
   static cudaError_t f3_n(const void* F2, int n_c, double* partial, long pbs, int batch, const void* tw,
                           cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = pen_bytes<N>(SH::TC3);
+    const size_t sm = col_bytes<N, SH::TC3, SH::E3>();
     auto k = k_f3<T, N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     int lo, nk1;
@@ -241,8 +242,8 @@ cudaError_t OpsRT<T>::p2(int N, const void* Ta, const void* Tb, void* W, int n_a
 }
 template <typename T>
 cudaError_t OpsRT<T>::p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
-                      const void* tw, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, st)));
+                      const void* tw, int* err, cudaStream_t st) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, err, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st) {
