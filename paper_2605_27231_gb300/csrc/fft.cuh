@@ -27,6 +27,11 @@ template <typename T> using cx = typename vec2<T>::type;
 template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
 template <typename T> __device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ cx<T> sub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// FP32: one paired (FP32x2) instruction per complex add / subtract (a - b as fma(b, -1, a), exact).
+template <> __device__ __forceinline__ cx<float> add<float>(cx<float> a, cx<float> b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ cx<float> sub<float>(cx<float> a, cx<float> b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 template <typename T> __device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
   return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -129,20 +134,24 @@ template <int N, int E> struct StockPlan {
 // Exchange buffers hold complex values (one 64-bit (FP32) or 128-bit (FP64) access per element) in two
 // ping-pong buffers, so a stage reads one buffer and writes the other with one barrier per stage.
 //
-// RowLayout: one pencil per group of P consecutive threads, private buffer, element p at p + p/16.
-//   Stage-0 writes (stride E between threads) and unit-stride reads then fall in distinct banks.
+// RowLayout: one pencil per group of P consecutive threads, private buffer, element p at p + p/2^PADSH.
+//   With PADSH = 3, stage-0 writes (stride E = 8 between threads), the span-8 writes of the middle stage
+//   and unit-stride reads fall in distinct banks within each 128-byte access phase; PADSH = 4 saves space
+//   at the cost of two-way conflicts on the middle-stage writes.
 // ColLayout<TC, E>: TC adjacent pencils (thread = j * TC + c) interleaved as [p][c]; rows are permuted
 //   within aligned groups of G = (128 B / element) / TC positions by g(p) = (p + p/E) mod G, so the G
 //   positions touched by one access phase of a warp (stride 1 or stride E) land on distinct banks.
-template <typename T, int N> struct RowLayout {
-  static constexpr int BUF = N + N / 16 + 1;  // elements per buffer
-  static constexpr int SIZE = 2 * BUF;        // elements per pencil (both buffers)
+template <typename T, int N, bool ONE = false, int PADSH = 3> struct RowLayout {
+  static constexpr bool SINGLE = ONE;                       // one buffer: a stage syncs between its reads and writes
+  static constexpr int BUF = N + (N - 1) / (1 << PADSH) + 1;  // elements per buffer
+  static constexpr int SIZE = ONE ? BUF : 2 * BUF;          // elements per pencil
   cx<T>* base;
-  __device__ __forceinline__ cx<T>* buf(int which) const { return base + which * BUF; }
-  __device__ __forceinline__ int idx(int p) const { return p + (p >> 4); }
+  __device__ __forceinline__ cx<T>* buf(int which) const { return ONE ? base : base + which * BUF; }
+  __device__ __forceinline__ int idx(int p) const { return p + (p >> PADSH); }
 };
 
 template <typename T, int N, int TC, int E> struct ColLayout {
+  static constexpr bool SINGLE = false;
   static constexpr int PER_PHASE = 128 / (int)sizeof(cx<T>);
   static constexpr int G0 = PER_PHASE / TC;
   static constexpr int G = G0 < 1 ? 1 : G0;
@@ -186,6 +195,7 @@ __device__ __forceinline__ void stock_stage(cx<T> (&v)[E], int j, const Lay& L, 
     const int k = jj & (Ns - 1);
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = rd[L.idx(jj + r * P)];
+    if constexpr (Lay::SINGLE) sync();
     constexpr int stride = N / (Ns * E);
 #pragma unroll
     for (int r = 1; r < E; ++r) v[r] = mul<T>(v[r], twiddle<T, DIR>(tw, r * k * stride));
