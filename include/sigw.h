@@ -149,10 +149,10 @@ sigw_status sigw_synchronize(sigw_plan plan);
 /* Human-readable text of a status code. */
 const char* sigw_strerror(sigw_status s);
 
-/* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 fused first + second inverse pass
- * (filter, gradients), 2 last inverse pass + product + first forward pass, 3 second forward pass,
- * 4 last forward pass + TT projection + shell sum, 5 bin finalisation. */
-#define SIGW_NKINDS 6
+/* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter,
+ * gradient), 2 second inverse pass, 3 last inverse pass + product + first forward pass, 4 second forward
+ * pass, 5 last forward pass + TT projection + shell sum, 6 bin finalisation. */
+#define SIGW_NKINDS 7
 typedef struct sigw_profile {
   double ms[SIGW_NKINDS];        /* summed CUDA-event durations (only while event timing is on) */
   double bytes[SIGW_NKINDS];     /* algorithmic bytes: each input element read once, each output written once */

@@ -41,10 +41,10 @@ int auto_alpha_batch(const sigw_opts& o) {
 
 // Sizes (bytes) of every device buffer of a plan.
 struct Sizes {
-  size_t phi, ring, ctl, W, synth, F, F2, partial, out, lut, tab, tw, amp, rows_sq;
+  size_t phi, T, W, synth, F, F2, partial, out, lut, tab, tw, amp, rows_sq;
   int maxblk;
   size_t total() const {
-    return phi + ring + ctl + std::max(W, synth) + F + F2 + partial + out + lut + tab + tw + amp + rows_sq + 4096;
+    return phi + T + std::max(W, synth) + F + F2 + partial + out + lut + tab + tw + amp + rows_sq + 4096;
   }
 };
 
@@ -57,9 +57,7 @@ Sizes sizes_of(int N, const sigw_opts& o) {
   sigw::LaunchShape sh = o.precision == 64 ? sigw::OpsRT<double>::shape(N) : sigw::OpsRT<float>::shape(N);
   s.maxblk = sh.maxblk_f3;
   s.phi = mb * NN * NH * cel;
-  (void)B;
-  s.ring = o.precision == 64 ? sigw::OpsRT<double>::p12_ring_bytes(N) : sigw::OpsRT<float>::p12_ring_bytes(N);
-  s.ctl = 128 + 8 * mb * (size_t)N * o.n_alpha;  // >= 2 counters per round (rounds <= batch * slabs * n_alpha)
+  s.T = 2 * mb * (size_t)B * NN * H * cel;
   s.W = mb * 3 * (size_t)o.n_alpha * NN * H * cel;
   s.synth = mb * (NN * H * cel + NN * NH * cel + NN * (size_t)N * rel) + 1024;
   s.F = mb * 6 * NN * NH * cel;
@@ -99,8 +97,7 @@ struct sigw_plan_s {
   // device buffers
   std::vector<void*> allocs;
   void* d_phi = nullptr;
-  void* d_ring = nullptr;  // L2-sized ring of the fused first/second inverse pass
-  void* d_ctl = nullptr;   // its work counter and per-round completion counters
+  void* d_T = nullptr;     // first-pass output (two fields per term of an alpha batch)
   void* d_work = nullptr;  // W during the hot loop, synthesis scratch during sigw_generate / sigw_fft3d
   void* d_F = nullptr;
   void* d_F2 = nullptr;
@@ -401,8 +398,7 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
     ptr = reinterpret_cast<decltype(ptr)>(_q);              \
   } while (0)
   ALLOC(p->d_phi, p->sz.phi);
-  ALLOC(p->d_ring, p->sz.ring);
-  ALLOC(p->d_ctl, p->sz.ctl);
+  ALLOC(p->d_T, p->sz.T);
   ALLOC(p->d_work, std::max(p->sz.W, p->sz.synth));
   ALLOC(p->d_F, p->sz.F);
   ALLOC(p->d_F2, p->sz.F2);
@@ -582,6 +578,8 @@ sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, do
   const int n_alpha = p->opts.n_alpha, nm1 = p->opts.n_modes + 1;
   const size_t NN = (size_t)N * N;
   const size_t cel = p->celem();
+  void* Ta = p->d_T;
+  void* Tb = (char*)p->d_T + (size_t)batch * p->B * NN * H * cel;
   const long pbs = (long)ns * 2 * p->sz.maxblk;
   p->h2d += sizeof(int) * ns + sizeof(double) * ns;
   const double fieldb = (double)batch * NN * H * cel;  // one packed complex field per realisation batch
@@ -596,20 +594,22 @@ sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, do
     for (int n1 = n1lo; n1 < n1lo + nk1; ++n1)
       for (int n2 = 0; n2 <= n_c; ++n2) disk += (n1 * n1 + n2 * n2 <= n_c * n_c + n_c);
     for (int m = 0; m < 2; ++m) {
-      CKP(p, cudaMemsetAsync(p->d_ctl, 0, p->sz.ctl, st), "clear work counters");
-      RUN(p, 1, phib + 3.0 * n_alpha * fieldb, "P12",
-          OPS(p, p12, N, p->d_phi, p->d_ring, p->d_work, lut, p->d_phitab[m], nm1, n_alpha, batch, p->d_tw, p->d_ctl,
-              p->d_err, st));
-      RUN(p, 2, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
+      for (int a0 = 0; a0 < n_alpha; a0 += p->B) {
+        const int nb = std::min(p->B, n_alpha - a0);
+        RUN(p, 1, phib + 2.0 * nb * fieldb, "P1",
+            OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, st));
+        RUN(p, 2, 5.0 * nb * fieldb, "P2", OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, st));
+      }
+      RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
           OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, st));
-      RUN(p, 3, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
+      RUN(p, 4, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
           OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st));
-      RUN(p, 4, 6.0 * batch * (double)N * disk * cel, "F3",
+      RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3",
           OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st));
     }
   }
   const sigw::LaunchShape shp = OPS(p, shape, N);
-  RUN(p, 5, (double)batch * ns * 2 * p->sz.maxblk * 8, "bin finalise",
+  RUN(p, 6, (double)batch * ns * 2 * p->sz.maxblk * 8, "bin finalise",
       sigw::launch_fin(p->d_partial, pbs, p->sz.maxblk, ns, p->d_shells, p->d_Nk, N, p->L, shp.tc_f3,
                        dev_out ? dev_out : p->d_out, batch, st));
   return SIGW_OK;

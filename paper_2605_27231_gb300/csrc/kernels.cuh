@@ -402,10 +402,11 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
 //   W[0] = IDFT_1[Ta]            (G_2 after i n2 and the last pass)
 //   W[1] = IDFT_1[i n1^D Ta]     (G_1)
 //   W[2] = IDFT_1[Tb]            (G_0)
+// One value array is live at a time (the Ta tile is reloaded through L1 for the second transform).
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
-                                            cx<T>* __restrict__ W, int n_alpha, int alpha0, int nb,
-                                            const cx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(256, 2) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
+                                               cx<T>* __restrict__ W, int n_alpha, int alpha0, int nb,
+                                               const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
   using Lay = ColLayout<T, N, TC, E>;
@@ -419,24 +420,26 @@ __global__ void __launch_bounds__(256) k_p2(const cx<T>* __restrict__ Ta, const 
   const long off = (long)a0 * N * H + cc;
   const cx<T>* ta = Ta + ((long)b * nb + a) * fstride + off;
   const cx<T>* tb = Tb + ((long)b * nb + a) * fstride + off;
-  cx<T> v[E], w[E];
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    v[r] = ta[(long)(j + r * P) * H];
-    const T nd = (T)derivn(j + r * P, N);
-    w[r] = mk<T>(-nd * v[r].y, nd * v[r].x);
-  }
   auto wout = [&](int f) { return W + (((long)b * 3 + f) * n_alpha + alpha0 + a) * fstride + off; };
+  cx<T> v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) v[r] = __ldg(ta + (long)(j + r * P) * H);
   fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
   cx<T>* o0 = wout(0);
 #pragma unroll
   for (int r = 0; r < E; ++r) o0[(long)(j + r * P) * H] = v[r];
-  fft_pencil<T, N, E, +1, Lay, SyncBlock>(w, j, L, tw, SyncBlock());
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const cx<T> x = __ldg(ta + (long)(j + r * P) * H);
+    const T nd = (T)derivn(j + r * P, N);
+    v[r] = mk<T>(-nd * x.y, nd * x.x);
+  }
+  fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
   cx<T>* o1 = wout(1);
 #pragma unroll
-  for (int r = 0; r < E; ++r) o1[(long)(j + r * P) * H] = w[r];
+  for (int r = 0; r < E; ++r) o1[(long)(j + r * P) * H] = v[r];
 #pragma unroll
-  for (int r = 0; r < E; ++r) v[r] = tb[(long)(j + r * P) * H];
+  for (int r = 0; r < E; ++r) v[r] = __ldg(tb + (long)(j + r * P) * H);
   fft_pencil<T, N, E, +1, Lay, SyncBlock, false>(v, j, L, tw, SyncBlock());
   cx<T>* o2 = wout(2);
 #pragma unroll
@@ -662,230 +665,6 @@ __global__ void __launch_bounds__(P3Cfg<T, N>::THREADS, 1) k_p3(const cx<T>* __r
       f2[k] = mk<T>((T)0.5 * (zk.y - zm.y), (T)-0.5 * (zk.x - zm.x));
     }
     Sync()();
-  }
-}
-
-// ---------------------------------------------------------------- fused first + second inverse pass
-// One persistent launch per (shell, kernel) runs both strided inverse passes for every realisation, column
-// slab (TC packed columns) and term.  Work items are handed out in a fixed order by an atomic counter:
-//   round r = (b, slab, term);  P1 items of round r (RI k1 rows each) write the slab's intermediate into
-//   ring slot r % NSLOT;  P2 items of round r (RI a0 rows each) read it back (mostly from L2: only about D
-//   slabs are written in between) and write the three W fields.
-//   Group order: P1(0..D-1), then P2(0), P1(D), P2(1), P1(D+1), ...   with D IPG >= 512 items, NSLOT = 2 D,
-// so a P2 round is handed out about 2D - 1 groups after its P1 round and a slot is refilled about 2D + 1
-// groups after its last reader was handed out: with a few hundred resident CTAs the waits below rarely spin.
-// Every wait is on an item handed out earlier, so the schedule cannot deadlock however many CTAs are
-// resident; waits are bounded and set *err on expiry.
-struct P12Ctl {
-  unsigned int next;  // work counter
-  unsigned int pad[31];
-  // followed by p1_done[rounds], p2_done[rounds] (unsigned int), zeroed before each launch
-};
-
-template <typename T, int N> struct P12Cfg {
-  using SH = Shape<T, N>;
-  static constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
-  static constexpr int THREADS = TC * P;
-  static constexpr int RI = 2;                 // rows per item
-  static constexpr int IPG = N / RI;           // items per group
-  static constexpr int NSLAB = H / TC;
-  static constexpr size_t SLOT = 2ull * N * N * TC;  // complex values per ring slot (Ta, Tb)
-  static constexpr int D = (512 + IPG - 1) / IPG;    // P1 lead in groups
-  static constexpr int NSLOT = 2 * D;
-  static constexpr size_t SMEM_BASE = (size_t)ColLayout<T, N, TC, E>::SIZE * sizeof(cx<T>) + N * sizeof(cx<T>) +
-                                      N * sizeof(int) + 64;
-};
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ bool wait_count(const unsigned int* ctr, unsigned int target, int* err) {
-  const long long t0 = clock64();
-  while (true) {
-    if (ld_acquire(ctr) >= target) return true;
-    if (clock64() - t0 > (1ll << 31)) {
-      atomicOr(err, 2);
-      return false;
-    }
-    __nanosleep(256);
-  }
-}
-
-// Decode work item id -> (kind, round) for the P12 schedule; kind 0 means an empty slot.
-template <int D>
-__device__ __forceinline__ void p12_decode(long id, int IPG, int rounds, int* kind, int* r, int* it) {
-  const int g = (int)(id / IPG);
-  *it = (int)(id % IPG);
-  if (g < D) {
-    *kind = 1;
-    *r = g;
-  } else if (((g - D) & 1) == 0) {
-    *kind = 2;
-    *r = (g - D) / 2;
-  } else {
-    *kind = 1;
-    *r = (g - D - 1) / 2 + D;
-  }
-  if (*r >= rounds) *kind = 0;
-}
-
-template <typename T, int N>
-__global__ void __launch_bounds__(P12Cfg<T, N>::THREADS, 2) k_p12(const cx<T>* __restrict__ phi, cx<T>* __restrict__ ring,
-                                                               cx<T>* __restrict__ W, const int16_t* __restrict__ lut,
-                                                               const T* __restrict__ phitab, int nm1, int n_alpha,
-                                                               int batch, const cx<T>* __restrict__ tw,
-                                                               P12Ctl* __restrict__ ctl, int* __restrict__ err) {
-  using CF = P12Cfg<T, N>;
-  constexpr int E = CF::E, P = CF::P, TC = CF::TC, H = N / 2, NH = H + 1, RI = CF::RI, IPG = CF::IPG;
-  constexpr int NSLAB = CF::NSLAB, NSLOT = CF::NSLOT;
-  using Lay = ColLayout<T, N, TC, E>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(smraw) + Lay::SIZE;
-  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);
-  int* sm_item = sm_cn + N;
-  T* sm_tab = reinterpret_cast<T*>(sm_item + 16);
-  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
-  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
-  unsigned int* p1_done = reinterpret_cast<unsigned int*>(ctl + 1);
-  const int rounds = batch * NSLAB * n_alpha;
-  unsigned int* p2_done = p1_done + rounds;
-  constexpr int D = CF::D;
-  const long total = (long)(2 * rounds + D) * IPG;
-  const long fstride = (long)N * N * H;
-  // Thread 0 fetches the next item and polls its dependency once while the current item computes, so
-  // the serial part between items is two barriers in the common case.
-  auto dep_of = [&](int kind, int r, const unsigned int** ctr) -> bool {  // does the item have a dependency?
-    if (kind == 1 && r >= NSLOT) {
-      *ctr = p2_done + (r - NSLOT);
-      return true;
-    }
-    if (kind == 2) {
-      *ctr = p1_done + r;
-      return true;
-    }
-    return false;
-  };
-  if (threadIdx.x == 0) {
-    sm_item[0] = (int)atomicAdd(&ctl->next, 1u);
-    sm_item[1] = 0;  // dependency of the fetched item not yet seen satisfied
-  }
-  while (true) {
-    __syncthreads();  // previous item finished with shared memory; sm_item holds the next item
-    const long id = sm_item[0];
-    const bool dep_seen = sm_item[1] != 0;
-    if (id >= total) break;
-    int kind, r, it;
-    p12_decode<D>(id, IPG, rounds, &kind, &r, &it);
-    __syncthreads();  // everyone has read sm_item
-    if (threadIdx.x == 0) {
-      const unsigned int* ctr;
-      if (!dep_seen && kind != 0 && dep_of(kind, r, &ctr)) wait_count(ctr, IPG, err);
-      const long nid = (long)atomicAdd(&ctl->next, 1u);
-      sm_item[0] = (int)nid;
-      int nk, nr, nit;
-      p12_decode<D>(nid, IPG, rounds, &nk, &nr, &nit);
-      const unsigned int* nctr;
-      sm_item[1] = (nid < total && nk != 0 && dep_of(nk, nr, &nctr)) ? (ld_acquire(nctr) >= (unsigned)IPG) : 1;
-    }
-    if (kind == 0) continue;
-    const int a = r % n_alpha;
-    const int slab = (r / n_alpha) % NSLAB;
-    const int b = r / (n_alpha * NSLAB);
-    cx<T>* slot = ring + (size_t)(r % NSLOT) * CF::SLOT;  // [2][a0][k1][TC]
-    const int cc = slab * TC + c;
-    if (kind == 1) {
-      // ---- first pass (the slot is free: P2 of round r - NSLOT is done)
-      for (int i = threadIdx.x; i < nm1; i += blockDim.x) sm_tab[i] = phitab[(long)a * nm1 + i];
-      __syncthreads();
-      for (int rr = 0; rr < RI; ++rr) {
-        const int k1 = it * RI + rr;
-        const int n1 = wrapn(k1, N);
-        const cx<T>* pb = phi + ((long)b * N * N + k1) * NH;
-        if (slab == 0) {
-          for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
-            const int n0 = wrapn(k0, N);
-            sm_nyq[k0] = __ldg(pb + (long)k0 * N * NH + H);
-            sm_cn[k0] = lut[n0 * n0 + n1 * n1 + H * H];
-          }
-          __syncthreads();
-        }
-        // V = phi_a(cell) Phi~ (column 0 packs k2 = 0 and k2 = H); the second transform (i n0 V) rebuilds V
-        // from the cached loads instead of keeping both arrays live
-        auto build = [&](cx<T>(&v)[E], bool grad) {
-#pragma unroll
-          for (int q = 0; q < E; ++q) {
-            const int k0 = j + q * P;
-            const int n0 = wrapn(k0, N);
-            const cx<T> ph = __ldg(pb + (long)k0 * N * NH + cc);
-            const T f = sm_tab[lut[n0 * n0 + n1 * n1 + cc * cc]];
-            cx<T> x = mk<T>(f * ph.x, f * ph.y);
-            if (cc == 0) {
-              const T fn = sm_tab[sm_cn[k0]];
-              const cx<T> yn = sm_nyq[k0];
-              x = mk<T>(x.x - fn * yn.y, x.y + fn * yn.x);
-            }
-            if (grad) {
-              const T nd = (T)derivn(k0, N);
-              x = mk<T>(-nd * x.y, nd * x.x);
-            }
-            v[q] = x;
-          }
-        };
-        cx<T> v[E];
-        build(v, false);
-        fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
-        cx<T>* ta = slot + (long)k1 * TC + c;  // [0][a0][k1][c]
-#pragma unroll
-        for (int q = 0; q < E; ++q) ta[(long)(j + q * P) * N * TC] = v[q];
-        build(v, true);
-        fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
-        cx<T>* tb = slot + (long)N * N * TC + (long)k1 * TC + c;
-#pragma unroll
-        for (int q = 0; q < E; ++q) tb[(long)(j + q * P) * N * TC] = v[q];
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) red_release_add(p1_done + r, 1u);
-    } else {
-      // ---- second pass (all first-pass items of this round are done)
-      __syncthreads();
-      for (int rr = 0; rr < RI; ++rr) {
-        const int a0 = it * RI + rr;
-        const cx<T>* ta = slot + (long)a0 * N * TC + c;
-        const cx<T>* tb = ta + (long)N * N * TC;
-        const long off = (long)a0 * N * H + cc;
-        auto wout = [&](int f) { return W + (((long)b * 3 + f) * n_alpha + a) * fstride + off; };
-        cx<T> v[E];
-#pragma unroll
-        for (int q = 0; q < E; ++q) v[q] = __ldcg(ta + (long)(j + q * P) * TC);
-        fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
-        cx<T>* o0 = wout(0);
-#pragma unroll
-        for (int q = 0; q < E; ++q) __stcs(o0 + (long)(j + q * P) * H, v[q]);
-#pragma unroll
-        for (int q = 0; q < E; ++q) {  // i n1 Ta (reloaded from L2)
-          const cx<T> x = __ldcg(ta + (long)(j + q * P) * TC);
-          const T nd = (T)derivn(j + q * P, N);
-          v[q] = mk<T>(-nd * x.y, nd * x.x);
-        }
-        fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
-        cx<T>* o1 = wout(1);
-#pragma unroll
-        for (int q = 0; q < E; ++q) __stcs(o1 + (long)(j + q * P) * H, v[q]);
-#pragma unroll
-        for (int q = 0; q < E; ++q) v[q] = __ldcg(tb + (long)(j + q * P) * TC);
-        fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
-        cx<T>* o2 = wout(2);
-#pragma unroll
-        for (int q = 0; q < E; ++q) __stcs(o2 + (long)(j + q * P) * H, v[q]);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) red_release_add(p2_done + r, 1u);
-    }
   }
 }
 

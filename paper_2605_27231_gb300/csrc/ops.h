@@ -43,12 +43,6 @@ struct OpsRT {
   // second inverse pass (axis 1), three outputs per term
   static cudaError_t p2(int N, const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
                         const void* tw, cudaStream_t st);
-  // first + second inverse pass fused in one persistent launch over all terms and realisations; the
-  // intermediate lives in an L2-sized ring (`ring`, p12_ring_bytes(N) bytes).  ctl: 128 bytes + 8 bytes per
-  // round (batch * slabs * n_alpha rounds), zeroed before the launch.
-  static cudaError_t p12(int N, const void* phi, void* ring, void* W, const int16_t* lut, const void* phitab, int nm1,
-                         int n_alpha, int batch, const void* tw, void* ctl, int* err, cudaStream_t st);
-  static size_t p12_ring_bytes(int N);
   // last inverse pass (axis 2, C2R) + sum_a sigma_a g_i g_j + forward R2C along axis 2 keeping k2 <= n_c
   // err: device int, OR-ed with 1 when a bounded wait of the bulk-copy pipeline gives up
   static cudaError_t p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,

@@ -93,27 +93,6 @@ struct OpsT {
     k<<<grid, CF::THREADS, CF::SMEM, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw, err);
     return cudaGetLastError();
   }
-  template <int N>
-  static cudaError_t p12_n(const void* phi, void* ring, void* W, const int16_t* lut, const void* phitab, int nm1,
-                           int n_alpha, int batch, const void* tw, void* ctl, int* err, cudaStream_t st) {
-    using CF = P12Cfg<T, N>;
-    const size_t sm = CF::SMEM_BASE + (size_t)nm1 * sizeof(T);
-    auto k = k_p12<T, N>;
-    SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
-    int dev = 0, nsm = 0, per = 0;
-    SIGW_CHECK_LAUNCH(cudaGetDevice(&dev));
-    SIGW_CHECK_LAUNCH(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SIGW_CHECK_LAUNCH(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, CF::THREADS, sm));
-    if (per < 1) per = 1;
-    const long items = (long)(2 * batch * CF::NSLAB * n_alpha + CF::D) * CF::IPG;
-    long grid = (long)nsm * per;
-    if (grid > items) grid = items;
-    k<<<(int)grid, CF::THREADS, sm, st>>>((const C*)phi, (C*)ring, (C*)W, lut, (const T*)phitab, nm1, n_alpha, batch,
-                                         (const C*)tw, (P12Ctl*)ctl, err);
-    return cudaGetLastError();
-  }
-  template <int N>
-  static size_t p12_ring_bytes_n() { return (size_t)P12Cfg<T, N>::NSLOT * P12Cfg<T, N>::SLOT * sizeof(C); }
   static void n1_range(int N, int n_c, int* lo, int* nk1) {
     const int H = N / 2;
     const int a = n_c < H - 1 ? -n_c : -H + 1;
@@ -265,23 +244,6 @@ template <typename T>
 cudaError_t OpsRT<T>::p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
                       const void* tw, int* err, cudaStream_t st) {
   SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, err, st)));
-}
-template <typename T>
-cudaError_t OpsRT<T>::p12(int N, const void* phi, void* ring, void* W, const int16_t* lut, const void* phitab, int nm1,
-                       int n_alpha, int batch, const void* tw, void* ctl, int* err, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template p12_n<NN>(phi, ring, W, lut, phitab, nm1, n_alpha, batch, tw, ctl, err, st)));
-}
-template <typename T>
-size_t OpsRT<T>::p12_ring_bytes(int N) {
-  switch (N) {
-    case 8: return OpsT<T>::template p12_ring_bytes_n<8>();
-    case 16: return OpsT<T>::template p12_ring_bytes_n<16>();
-    case 32: return OpsT<T>::template p12_ring_bytes_n<32>();
-    case 64: return OpsT<T>::template p12_ring_bytes_n<64>();
-    case 128: return OpsT<T>::template p12_ring_bytes_n<128>();
-    case 256: return OpsT<T>::template p12_ring_bytes_n<256>();
-    default: return OpsT<T>::template p12_ring_bytes_n<512>();
-  }
 }
 template <typename T>
 cudaError_t OpsRT<T>::f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st) {

@@ -37,8 +37,8 @@ class NGMap(C.Structure):
     _fields_ = [("kind", C.c_int), ("F_NL", C.c_double), ("G_NL", C.c_double), ("usr_floor", C.c_double)]
 
 
-NKINDS = 6
-KINDS = ("synth", "p12_inv_axis0_axis1_filter", "p3_inv_axis2_product_fwd_axis2", "f2_fwd_axis1",
+NKINDS = 7
+KINDS = ("synth", "p1_inv_axis0_filter", "p2_inv_axis1", "p3_inv_axis2_product_fwd_axis2", "f2_fwd_axis1",
          "f3_fwd_axis0_tt_bin", "bin_finalise")
 
 
