@@ -176,6 +176,24 @@ sigw_status sigw_decompose(const sigw_opts* opts, int m, double* sigma, double* 
  * u = sqrt(msq)/n_c, decided on squares ((e_i n_c)^2 <= msq in FP64), or n_modes outside [umin, umax). */
 sigw_status sigw_cell_table(const sigw_opts* opts, int n_c, int msq_max, int16_t* lut);
 
+/* The paper has no counterpart to this entry point: it is a library utility.
+ * sigw_fft3d without a plan and without any device allocation, for callers that cannot call cudaMalloc
+ * (for example a host program whose own pool allocator already owns all device memory, or a latency-critical
+ * path where a synchronising cudaMalloc is not acceptable).  Same transforms and layouts as sigw_fft3d:
+ * direction -1 real in[N][N][N] -> complex out[N][N][N/2+1], +1 the unnormalised inverse; precision 32 or 64.
+ * Scratch: file-scope device arrays of fixed size (8 MiB for the packed half spectrum, N*N*(N/2) complex
+ * values, plus 248-entry twiddle tables per precision), held by every GPU that loads the library until the
+ * process exits.  Limit: N*N*(N/2) complex values must fit in 8 MiB, i.e. N <= 128 in FP32 and N <= 64 in
+ * FP64 (N a power of two >= 8); larger N returns SIGW_EINVAL.  The first call on a device sets that device up
+ * (looks up the arrays' device addresses and fills the twiddles, synchronously); make that first call before
+ * any stream capture.  Work is queued on cuda_stream (NULL: the legacy default stream); the call does not
+ * wait.  All calls share the one scratch array, which keeps the last call's contents (every call overwrites
+ * all of what it reads, so nothing needs clearing): calls that overlap on the GPU (different streams, or a
+ * second call before the first finished on another stream) race and give wrong results.
+ * Errors: SIGW_EINVAL (arguments or size limit), SIGW_ECUDA (set-up or launch failed). */
+sigw_status sigw_fft3d_noalloc(int N, int precision, int direction, const void* in_dev, void* out_dev,
+                               void* cuda_stream);
+
 /* Test hook for failure handling: the next `n`-th device allocation made by the library fails with
  * SIGW_ENOMEM (n = 1: the next one; n <= 0 disables).  Affects the calling process only. */
 sigw_status sigw_debug_fail_alloc(int n);

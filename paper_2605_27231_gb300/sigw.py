@@ -79,6 +79,7 @@ def lib():
         "sigw_cell_table": (C.c_int, [C.POINTER(Opts), C.c_int, C.c_int, C.POINTER(C.c_int16)]),
         "sigw_debug_fail_alloc": (C.c_int, [C.c_int]),
         "sigw_plan_profile": (C.c_int, [P, C.c_int]),
+        "sigw_fft3d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P]),
         "sigw_plan_profile_read": (C.c_int, [P, C.POINTER(Profile)]),
     }
     for name, (res, args) in sig.items():
@@ -140,6 +141,12 @@ def footprint(N, opts=None):
     n = C.c_size_t(0)
     _check(lib().sigw_plan_footprint(N, C.byref(o), C.byref(n)))
     return n.value
+
+
+def fft3d_noalloc(N, precision, direction, in_ptr, out_ptr, stream=None):
+    """sigw_fft3d_noalloc: the 3-D real FFT with no plan and no device allocation (N <= 128 FP32, <= 64 FP64)."""
+    _check(lib().sigw_fft3d_noalloc(N, precision, direction, C.c_void_p(in_ptr), C.c_void_p(out_ptr),
+                                    C.c_void_p(stream) if stream else None), None, "sigw_fft3d_noalloc")
 
 
 def debug_fail_alloc(n):
