@@ -188,7 +188,7 @@ def run_ours(args):
             p64.spectrum_async(dev_out.data_ptr(), shells)
             b.record(stream)
             b.synchronize()
-            sh_ms = b and a.elapsed_time(b)
+            sh_ms = a.elapsed_time(b)
         per_spec_s = (gen_ms + sh_ms * n_sh / len(shells)) / 1e3
         fp64 = {"value": 1.0 / per_spec_s, "unit": "spectra/s", "dtype": "f64",
                 "sample": "1 seed, shells %s of 1..%d, extrapolated to all shells" % (shells.tolist(), n_sh),
