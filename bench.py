@@ -197,6 +197,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(spec, args.cpu_terms)
+    serving = None
+    if rank == 0 and args.serve_requests > 0:
+        serving = serving_run(args)
 
     if rank == 0:
         line = {
@@ -220,11 +223,60 @@ def run_ours(args):
             "clocks": clocks,
             "fp64_path": fp64,
             "cpu_baseline": cpu,
+            "serving": serving,
             "omega_finite_positive": omega_ok,
         }
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def serving_run(args):
+    """Poisson replay of mixed spectrum requests through the continuous-batching server (sigw_submit).
+
+    Service times of one request per size class (alone, plans resident) give the single-slot capacity;
+    requests then arrive at args.serve_load times that rate.  Latency = completion - submission."""
+    import numpy as np
+    from paper_2605_27231_gb300 import sigw
+    sizes = (64, 128, 256)
+    srv = sigw.Server(args.serve_budget_gb * 1e9, max_slots=args.serve_slots, max_batch=args.serve_batch,
+                      precision=32)
+    try:
+        service = {}
+        for N in sizes:  # warm plans, then time one request alone
+            spec = workloads.serving_stream(1, 1.0, seed=1, sizes=(N,))[0][1]
+            srv.wait(srv.submit(spec))
+            t0 = time.perf_counter()
+            srv.wait(srv.submit(spec))
+            service[N] = time.perf_counter() - t0
+        mean_service = sum(service.values()) / len(service)
+        rate = args.serve_load / mean_service
+        stream = workloads.serving_stream(args.serve_requests, rate, seed=7, sizes=sizes)
+        t_start = time.perf_counter()
+        tickets = []
+        for t_arr, spec in stream:
+            d = t_start + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append((spec.N, srv.submit(spec)))
+        lat = {N: [] for N in sizes}
+        for N, t in tickets:
+            om, l = srv.wait(t, timeout_s=1200)
+            lat[N].append(l)
+        t_end = time.perf_counter()
+        st = srv.stats()
+    finally:
+        srv.close()
+    allv = sorted(l for v in lat.values() for l in v)
+    pct = lambda v, q: float(np.percentile(v, q)) if v else None
+    return {"requests": len(allv), "arrival_rate_hz": rate, "load": args.serve_load,
+            "single_request_service_s": service, "spectra_per_s": len(allv) / (t_end - t_start),
+            "p50_latency_s": pct(allv, 50), "p99_latency_s": pct(allv, 99),
+            "per_size": {str(N): {"n": len(v), "p50_s": pct(v, 50), "p99_s": pct(v, 99)} for N, v in lat.items()},
+            "slots": args.serve_slots, "max_batch": args.serve_batch, "batches": st["batches"],
+            "hbm_peak_gb": st["hbm_peak"] / 1e9, "budget_gb": args.serve_budget_gb,
+            "mix": "N uniform over {64,128,256}; f_NL ~ U[-5,20]; sigma ~ U[0.1,1]; map uniform over "
+                   "{gauss, local, usr}; Poisson arrivals, seed 7; FP32"}
 
 
 def oracle_sample(spec, n_terms):
@@ -289,6 +341,11 @@ def main():
     ap.add_argument("--fp64-shells", type=int, default=4)
     ap.add_argument("--cpu-terms", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-batch", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -121,6 +121,12 @@ sigw_status sigw_plan_kernel_terms(sigw_plan plan, int m, double* sigma, double*
 sigw_status sigw_generate(sigw_plan plan, const sigw_pzeta* pz, const sigw_ngmap* map, const uint64_t* seeds,
                           int batch, int64_t* usr_hits);
 
+/* As sigw_generate, with its own P_zeta parameters and map per realisation: pz[batch], maps[batch].  A batch that
+ * mixes Gaussian and non-Gaussian members sends the Gaussian ones through the identity map (their Phi~ then
+ * differs from the Gaussian-only route by round-off).  Same errors as sigw_generate. */
+sigw_status sigw_generate_batch(sigw_plan plan, const sigw_pzeta* pz, const sigw_ngmap* maps, const uint64_t* seeds,
+                                int batch, int64_t* usr_hits);
+
 /* Envelopes, TT projection and shell binning (steps 3-4) for the realisations of the last sigw_generate.
  * shells: n_shells shell indices in [1, N/2] (NULL: all N/2 in order).  Host outputs, [batch][n_shells],
  * any may be NULL: omega (Omega_GW), PA, PB (P_A, P_B summed over polarisations), Nk (modes per shell).
@@ -148,6 +154,41 @@ sigw_status sigw_synchronize(sigw_plan plan);
 
 /* Human-readable text of a status code. */
 const char* sigw_strerror(sigw_status s);
+
+/* ---------------------------------------------------------------- serving
+ * A server keeps plans resident on the current device and batches spectrum requests as they arrive
+ * (continuous batching): max_slots worker threads each take the oldest admissible request together with
+ * queued requests of the same size class (N, L), up to opts->max_batch, and run them as one batch on a plan of
+ * a shared pool; plans own their streams, so slots overlap on the device.  A plan is created only if its
+ * footprint (sigw_plan_footprint) fits hbm_budget_bytes beside the resident plans; idle plans are evicted
+ * least-recently-used to make room, and only the oldest queued request may allocate (no starvation).
+ * All server calls are thread-safe.  No counterpart in the paper (which reports single timings,
+ * Sec. sec_conclusions); this is the serving layer around its method. */
+typedef struct sigw_server_stats {
+  uint64_t submitted, completed, failed, queued, batches, plans_created, plans_evicted, plans_resident;
+  size_t hbm_in_use, hbm_peak, hbm_budget;
+} sigw_server_stats;
+
+/* opts: plan options of every plan (NULL: defaults; max_batch is the per-batch cap).  Errors: SIGW_EINVAL. */
+sigw_status sigw_server_create(size_t hbm_budget_bytes, int max_slots, const sigw_opts* opts, sigw_server* out);
+
+/* "sigw_submit": queue one request (one seed); *ticket identifies it.  SIGW_EBUSY if a plan for N alone does not
+ * fit the budget (the request could never run); SIGW_EINVAL for bad arguments. */
+sigw_status sigw_submit(sigw_server srv, int N, double L, const sigw_pzeta* pz, const sigw_ngmap* map, uint64_t seed,
+                        uint64_t* ticket);
+
+/* Non-blocking: SIGW_ENOTREADY until the request is done; then copies Omega (N/2 doubles, nullable) and the
+ * latency (seconds from submission to completion, nullable), returns the request's status and forgets the
+ * ticket.  SIGW_EINVAL for an unknown ticket. */
+sigw_status sigw_poll(sigw_server srv, uint64_t ticket, double* omega, double* latency_s);
+
+/* As sigw_poll, but waits up to timeout_s seconds; SIGW_ETIMEOUT if the request is still not done. */
+sigw_status sigw_wait(sigw_server srv, uint64_t ticket, double timeout_s, double* omega, double* latency_s);
+
+sigw_status sigw_server_stats_read(sigw_server srv, sigw_server_stats* out);
+
+/* Finishes running batches, drops queued requests, frees every plan. */
+sigw_status sigw_server_destroy(sigw_server srv);
 
 /* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter,
  * gradient), 2 second inverse pass, 3 last inverse pass + product + first forward pass, 4 second forward

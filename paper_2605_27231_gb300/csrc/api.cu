@@ -68,7 +68,7 @@ Sizes sizes_of(int N, const sigw_opts& o) {
   s.lut = H * msq * sizeof(int16_t);
   s.tab = 2 * ((size_t)o.n_alpha * (o.n_modes + 1) + o.n_alpha) * rel;
   s.tw = (size_t)N * cel;
-  s.amp = msq * rel;
+  s.amp = mb * msq * rel + mb * sizeof(sigw::MapArgs);
   const int rb = o.precision == 64 ? sigw::OpsRT<double>::rows_blocks(N) : sigw::OpsRT<float>::rows_blocks(N);
   s.rows_sq = mb * ((size_t)rb * sizeof(double) + 2 * sizeof(double) + 2 * sizeof(uint64_t));
   return s;
@@ -109,7 +109,8 @@ struct sigw_plan_s {
   void* d_phitab[2] = {nullptr, nullptr};
   void* d_sigma[2] = {nullptr, nullptr};
   void* d_tw = nullptr;
-  void* d_amp = nullptr;
+  void* d_amp = nullptr;            // [max_batch][msq_max + 1] synthesis amplitudes
+  sigw::MapArgs* d_maps = nullptr;  // [max_batch] map parameters
   double* d_sq = nullptr;
   double* d_mean = nullptr;
   unsigned long long* d_hits = nullptr;
@@ -412,7 +413,8 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
     ALLOC(p->d_sigma[m], (size_t)o.n_alpha * rel);
   }
   ALLOC(p->d_tw, (size_t)N * cel);
-  ALLOC(p->d_amp, (p->msq_max + 1) * rel);
+  ALLOC(p->d_amp, mb * (p->msq_max + 1) * rel);
+  ALLOC(p->d_maps, mb * sizeof(sigw::MapArgs));
   const int rb = OPS(p, rows_blocks, N);
   ALLOC(p->d_sq, mb * rb * sizeof(double));
   ALLOC(p->d_mean, mb * sizeof(double));
@@ -481,31 +483,45 @@ sigw_status sigw_synchronize(sigw_plan p) {
   return check_err_flag(p);
 }
 
-sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* map, const uint64_t* seeds, int batch,
-                          int64_t* usr_hits) {
+sigw_status sigw_generate_batch(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* maps, const uint64_t* seeds,
+                                int batch, int64_t* usr_hits) {
   if (!p) return SIGW_EINVAL;
-  if (!pz || !map || !seeds || batch < 1 || batch > p->opts.max_batch)
+  if (!pz || !maps || !seeds || batch < 1 || batch > p->opts.max_batch)
     return fail(p, SIGW_EINVAL, "sigw_generate: bad arguments");
-  if (!(pz->A >= 0) || !(pz->sigma > 0) || !(pz->kstar > 0) || map->kind < 0 || map->kind > 2)
-    return fail(p, SIGW_EINVAL, "sigw_generate: bad P_zeta or map parameters");
-  const double floor = map->usr_floor > 0 ? map->usr_floor : 1e-6;
+  bool all_gauss = true, any_usr = false;
+  for (int b = 0; b < batch; ++b) {
+    if (!(pz[b].A >= 0) || !(pz[b].sigma > 0) || !(pz[b].kstar > 0) || maps[b].kind < 0 || maps[b].kind > 2)
+      return fail(p, SIGW_EINVAL, "sigw_generate: bad P_zeta or map parameters");
+    all_gauss = all_gauss && maps[b].kind == SIGW_MAP_GAUSS;
+    any_usr = any_usr || maps[b].kind == SIGW_MAP_USR;
+  }
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
   const int N = p->N, H = N / 2;
   const double L = p->L, dx = L / N, kf = 2.0 * kPi / L;
   const size_t NN = (size_t)N * N;
+  const size_t msq1 = p->msq_max + 1;
   // synthesis amplitude sqrt(P_zeta(k) dx^3) per integer |n|^2, P = 2 pi^2 Delta^2 / k^3 (Eq. eq_lognormal)
-  std::vector<double> amp(p->msq_max + 1, 0.0);
-  for (size_t msq = 1; msq <= p->msq_max; ++msq) {
-    const double k = kf * std::sqrt((double)msq);
-    const double lk = std::log(k / pz->kstar);
-    const double d2 = pz->A / std::sqrt(2.0 * kPi * pz->sigma * pz->sigma) * std::exp(-lk * lk / (2.0 * pz->sigma * pz->sigma));
-    const double P = 2.0 * kPi * kPi * d2 / (k * k * k);
-    amp[msq] = std::sqrt(P * dx * dx * dx);
+  std::vector<double> amp(batch * msq1, 0.0);
+  std::vector<sigw::MapArgs> margs(batch);
+  for (int b = 0; b < batch; ++b) {
+    for (size_t msq = 1; msq <= p->msq_max; ++msq) {
+      const double k = kf * std::sqrt((double)msq);
+      const double lk = std::log(k / pz[b].kstar);
+      const double sg = pz[b].sigma;
+      const double d2 = pz[b].A / std::sqrt(2.0 * kPi * sg * sg) * std::exp(-lk * lk / (2.0 * sg * sg));
+      const double P = 2.0 * kPi * kPi * d2 / (k * k * k);
+      amp[b * msq1 + msq] = std::sqrt(P * dx * dx * dx);
+    }
+    margs[b] = sigw::MapArgs{maps[b].kind, maps[b].F_NL, maps[b].G_NL,
+                             maps[b].usr_floor > 0 ? maps[b].usr_floor : 1e-6};
   }
   std::vector<unsigned char> buf;
   convert(amp, p->opts.precision, buf);
   CKP(p, cudaMemcpyAsync(p->d_amp, buf.data(), buf.size(), cudaMemcpyHostToDevice, p->st), "upload amp");
+  CKP(p, cudaMemcpyAsync(p->d_maps, margs.data(), sizeof(sigw::MapArgs) * batch, cudaMemcpyHostToDevice, p->st),
+      "upload maps");
   CKP(p, cudaMemcpyAsync(p->d_seeds, seeds, sizeof(uint64_t) * batch, cudaMemcpyHostToDevice, p->st), "upload seeds");
+  p->h2d += buf.size() + sizeof(uint64_t) * batch + sizeof(sigw::MapArgs) * batch;
   const size_t cel = p->celem();
   char* work = (char*)p->d_work;
   void* Y = work;
@@ -514,14 +530,14 @@ sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* m
   cudaStream_t st = p->st;
   const double Yb = (double)batch * NN * H * cel, Xb = (double)batch * NN * (H + 1) * cel;
   const double Rb = (double)batch * NN * N * p->relem();
-  p->h2d += buf.size() + sizeof(uint64_t) * batch;
   RUN(p, 0, Yb, "noise + rows R2C", OPS(p, rows_r2c_noise, N, Y, p->d_seeds, batch, p->d_tw, st));
   RUN(p, 0, 2 * Yb, "forward axis 1", OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st));
   RUN(p, 0, 2 * Yb, "forward axis 0", OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st));
-  if (map->kind == SIGW_MAP_GAUSS) {
-    RUN(p, 0, Yb + Xb, "unpack (Gaussian Phi)", OPS(p, unpack, N, Y, p->d_phi, batch, p->d_amp, 2.0 / 3.0, 0, st));
-  } else {
-    RUN(p, 0, Yb + Xb, "unpack (zeta_g)", OPS(p, unpack, N, Y, X, batch, p->d_amp, 1.0, 0, st));
+  if (all_gauss) {
+    RUN(p, 0, Yb + Xb, "unpack (Gaussian Phi)",
+        OPS(p, unpack, N, Y, p->d_phi, batch, p->d_amp, (long)msq1, 2.0 / 3.0, 0, st));
+  } else {  // Gaussian members of a mixed batch go through the identity map
+    RUN(p, 0, Yb + Xb, "unpack (zeta_g)", OPS(p, unpack, N, Y, X, batch, p->d_amp, (long)msq1, 1.0, 0, st));
     RUN(p, 0, Yb + Xb, "pack", OPS(p, pack, N, X, Y, batch, st));
     RUN(p, 0, 2 * Yb, "inverse axis 0", OPS(p, pass, N, Y, 0, +1, batch, p->d_tw, st));
     RUN(p, 0, 2 * Yb, "inverse axis 1", OPS(p, pass, N, Y, 1, +1, batch, p->d_tw, st));
@@ -531,14 +547,15 @@ sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* m
     RUN(p, 0, (double)batch * rb * 8, "mean zeta_g^2",
         sigw::launch_reduce_mean(p->d_sq, rb, p->d_mean, batch, 1.0 / ((double)NN * N), st));
     CKP(p, cudaMemsetAsync(p->d_hits, 0, sizeof(unsigned long long) * batch, st), "memset hits");
-    sigw::MapArgs ma{map->kind, map->F_NL, map->G_NL, floor};
-    RUN(p, 0, Rb + Yb, "map + rows R2C", OPS(p, rows_r2c_map, N, R, Y, batch, ma, p->d_mean, p->d_hits, p->d_tw, st));
+    RUN(p, 0, Rb + Yb, "map + rows R2C",
+        OPS(p, rows_r2c_map, N, R, Y, batch, p->d_maps, p->d_mean, p->d_hits, p->d_tw, st));
     RUN(p, 0, 2 * Yb, "forward axis 1", OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st));
     RUN(p, 0, 2 * Yb, "forward axis 0", OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st));
-    RUN(p, 0, Yb + Xb, "unpack (Phi)", OPS(p, unpack, N, Y, p->d_phi, batch, nullptr, (2.0 / 3.0) * dx * dx * dx, 1, st));
+    RUN(p, 0, Yb + Xb, "unpack (Phi)",
+        OPS(p, unpack, N, Y, p->d_phi, batch, nullptr, 0L, (2.0 / 3.0) * dx * dx * dx, 1, st));
   }
   std::vector<unsigned long long> hits(batch, 0);
-  if (map->kind == SIGW_MAP_USR) {
+  if (any_usr) {
     CKP(p, cudaMemcpyAsync(hits.data(), p->d_hits, sizeof(unsigned long long) * batch, cudaMemcpyDeviceToHost, st),
         "download hits");
     p->d2h += sizeof(unsigned long long) * batch;
@@ -552,6 +569,15 @@ sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* m
   }
   if (any && p->opts.strict_domain) return fail(p, SIGW_EDOMAIN, "USR floor hits in strict mode");
   return SIGW_OK;
+}
+
+sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* map, const uint64_t* seeds, int batch,
+                          int64_t* usr_hits) {
+  if (!p) return SIGW_EINVAL;
+  if (!pz || !map || batch < 1 || batch > 64) return fail(p, SIGW_EINVAL, "sigw_generate: bad arguments");
+  std::vector<sigw_pzeta> pzs(batch, *pz);
+  std::vector<sigw_ngmap> ms(batch, *map);
+  return sigw_generate_batch(p, pzs.data(), ms.data(), seeds, batch, usr_hits);
 }
 
 sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, double* dev_out) {
@@ -662,7 +688,7 @@ sigw_status sigw_fft3d(sigw_plan p, int direction, const void* in_dev, void* out
     RUN(p, 0, 0, "rows R2C", OPS(p, rows_r2c_real, N, in_dev, Y, 1, p->d_tw, st));
     RUN(p, 0, 0, "forward axis 1", OPS(p, pass, N, Y, 1, -1, 1, p->d_tw, st));
     RUN(p, 0, 0, "forward axis 0", OPS(p, pass, N, Y, 0, -1, 1, p->d_tw, st));
-    RUN(p, 0, 0, "unpack", OPS(p, unpack, N, Y, out_dev, 1, nullptr, 1.0, 1, st));
+    RUN(p, 0, 0, "unpack", OPS(p, unpack, N, Y, out_dev, 1, nullptr, 0L, 1.0, 1, st));
   } else {
     RUN(p, 0, 0, "pack", OPS(p, pack, N, in_dev, Y, 1, st));
     RUN(p, 0, 0, "inverse axis 0", OPS(p, pass, N, Y, 0, +1, 1, p->d_tw, st));

@@ -86,7 +86,7 @@ template <> struct RowSync<128> { using type = SyncBlock; };
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>* __restrict__ Y,
                                                   const cx<T>* __restrict__ tw, const uint64_t* __restrict__ seeds,
-                                                  MapArgs map, const double* __restrict__ mean,
+                                                  const MapArgs* __restrict__ maps, const double* __restrict__ mean,
                                                   unsigned long long* __restrict__ hits) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ER, P = SH::PR, H = N / 2;
@@ -103,7 +103,11 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>
   cx<T> v[E];
   unsigned long long myhits = 0;
   double mu = 0.0;
-  if (MODE == 2) mu = mean[b];
+  MapArgs map{0, 0.0, 0.0, 0.0};
+  if (MODE == 2) {
+    mu = mean[b];
+    map = maps[b];
+  }
 #pragma unroll
   for (int r = 0; r < E; ++r) {
     const int x = j + r * P;
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(256) k_pass(cx<T>* __restrict__ Y, const cx<T>
 // MODE 1: times factor.
 template <typename T, int MODE>
 __global__ void k_unpack(const cx<T>* __restrict__ Y, cx<T>* __restrict__ X, int N, const T* __restrict__ amp,
-                         T factor, long total) {
+                         long amp_bstride, T factor, long total) {
   const int H = N / 2, NH = H + 1;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int k2 = (int)(i % NH);
@@ -289,7 +293,7 @@ __global__ void k_unpack(const cx<T>* __restrict__ Y, cx<T>* __restrict__ X, int
       const int n0 = wrapn(k0, N), n1 = wrapn(k1, N);
       const int msq = n0 * n0 + n1 * n1 + k2 * k2;
       const bool zero = (k0 == H) || (k1 == H) || (k2 == H) || msq == 0;
-      const T a = zero ? (T)0 : amp[msq] * factor;
+      const T a = zero ? (T)0 : amp[b * amp_bstride + msq] * factor;
       val = mk<T>(val.x * a, val.y * a);
     } else {
       val = mk<T>(val.x * factor, val.y * factor);

@@ -88,7 +88,7 @@ cudaError_t run_fft(int N, int direction, const void* in, void* out, void* scrat
     if ((e = O::rows_r2c_real(N, in, scratch, 1, tw, st)) != cudaSuccess) return e;
     if ((e = O::pass(N, scratch, 1, -1, 1, tw, st)) != cudaSuccess) return e;
     if ((e = O::pass(N, scratch, 0, -1, 1, tw, st)) != cudaSuccess) return e;
-    return O::unpack(N, scratch, out, 1, nullptr, 1.0, 1, st);
+    return O::unpack(N, scratch, out, 1, nullptr, 0, 1.0, 1, st);
   }
   if ((e = O::pack(N, in, scratch, 1, st)) != cudaSuccess) return e;
   if ((e = O::pass(N, scratch, 0, +1, 1, tw, st)) != cudaSuccess) return e;

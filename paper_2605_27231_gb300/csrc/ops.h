@@ -24,14 +24,16 @@ struct OpsRT {
   // ---- synthesis chain (packed layout [b][a0][a1][N/2], standard layout [b][k0][k1][N/2+1])
   static cudaError_t rows_r2c_noise(int N, void* Y, const uint64_t* seeds, int batch, const void* tw, cudaStream_t st);
   static cudaError_t rows_r2c_real(int N, const void* R, void* Y, int batch, const void* tw, cudaStream_t st);
-  static cudaError_t rows_r2c_map(int N, const void* R, void* Y, int batch, MapArgs map, const double* mean,
+  // map: device array of per-realisation MapArgs
+  static cudaError_t rows_r2c_map(int N, const void* R, void* Y, int batch, const MapArgs* map, const double* mean,
                                   unsigned long long* hits, const void* tw, cudaStream_t st);
   static cudaError_t rows_c2r(int N, const void* Y, void* R, int batch, double scale, double* sq_partial,
                               const void* tw, cudaStream_t st);
   static cudaError_t pass(int N, void* Y, int axis, int dir, int batch, const void* tw, cudaStream_t st);
-  // mode 0: times amp[|n|^2] * factor and zero on k = 0 and the Nyquist planes; mode 1: times factor
-  static cudaError_t unpack(int N, const void* Y, void* X, int batch, const void* amp, double factor, int mode,
-                            cudaStream_t st);
+  // mode 0: times amp[b * amp_bstride + |n|^2] * factor and zero on k = 0 and the Nyquist planes;
+  // mode 1: times factor
+  static cudaError_t unpack(int N, const void* Y, void* X, int batch, const void* amp, long amp_bstride, double factor,
+                            int mode, cudaStream_t st);
   static cudaError_t pack(int N, const void* X, void* Y, int batch, cudaStream_t st);
   static int rows_blocks(int N);  // CTAs per realisation of rows_c2r (entries of sq_partial per realisation)
   static LaunchShape shape(int N);

@@ -28,7 +28,7 @@ struct OpsT {
 
   // ------------------------------------------------------------ synthesis
   template <int N, int MODE>
-  static cudaError_t rows_r2c_n(const void* R, void* Y, const uint64_t* seeds, MapArgs map, const double* mean,
+  static cudaError_t rows_r2c_n(const void* R, void* Y, const uint64_t* seeds, const MapArgs* map, const double* mean,
                                 unsigned long long* hits, int batch, const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
     const size_t sm = row_bytes<N>(SH::RPC);
@@ -153,16 +153,14 @@ struct OpsT {
 
 template <typename T>
 cudaError_t OpsRT<T>::rows_r2c_noise(int N, void* Y, const uint64_t* seeds, int batch, const void* tw, cudaStream_t st) {
-  MapArgs m{0, 0, 0, 0};
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 1>(nullptr, Y, seeds, m, nullptr, nullptr, batch, tw, st)));
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 1>(nullptr, Y, seeds, nullptr, nullptr, nullptr, batch, tw, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::rows_r2c_real(int N, const void* R, void* Y, int batch, const void* tw, cudaStream_t st) {
-  MapArgs m{0, 0, 0, 0};
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 0>(R, Y, nullptr, m, nullptr, nullptr, batch, tw, st)));
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 0>(R, Y, nullptr, nullptr, nullptr, nullptr, batch, tw, st)));
 }
 template <typename T>
-cudaError_t OpsRT<T>::rows_r2c_map(int N, const void* R, void* Y, int batch, MapArgs map, const double* mean,
+cudaError_t OpsRT<T>::rows_r2c_map(int N, const void* R, void* Y, int batch, const MapArgs* map, const double* mean,
                                 unsigned long long* hits, const void* tw, cudaStream_t st) {
   SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 2>(R, Y, nullptr, map, mean, hits, batch, tw, st)));
 }
@@ -184,16 +182,17 @@ cudaError_t OpsRT<T>::pass(int N, void* Y, int axis, int dir, int batch, const v
   return cudaErrorInvalidValue;
 }
 template <typename T>
-cudaError_t OpsRT<T>::unpack(int N, const void* Y, void* X, int batch, const void* amp, double factor, int mode,
-                          cudaStream_t st) {
+cudaError_t OpsRT<T>::unpack(int N, const void* Y, void* X, int batch, const void* amp, long amp_bstride,
+                          double factor, int mode, cudaStream_t st) {
   const long total = (long)batch * N * N * (N / 2 + 1);
   const int thr = 256;
   long blocks = (total + thr - 1) / thr;
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (mode == 0)
-    k_unpack<T, 0><<<(int)blocks, thr, 0, st>>>((const cx<T>*)Y, (cx<T>*)X, N, (const T*)amp, (T)factor, total);
+    k_unpack<T, 0><<<(int)blocks, thr, 0, st>>>((const cx<T>*)Y, (cx<T>*)X, N, (const T*)amp, amp_bstride, (T)factor,
+                                               total);
   else
-    k_unpack<T, 1><<<(int)blocks, thr, 0, st>>>((const cx<T>*)Y, (cx<T>*)X, N, nullptr, (T)factor, total);
+    k_unpack<T, 1><<<(int)blocks, thr, 0, st>>>((const cx<T>*)Y, (cx<T>*)X, N, nullptr, 0, (T)factor, total);
   return cudaGetLastError();
 }
 template <typename T>

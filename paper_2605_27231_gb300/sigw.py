@@ -47,6 +47,12 @@ class Profile(C.Structure):
                 ("h2d_bytes", C.c_double), ("d2h_bytes", C.c_double)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "queued", "batches", "plans_created",
+                                          "plans_evicted", "plans_resident")] + \
+               [(n, C.c_size_t) for n in ("hbm_in_use", "hbm_peak", "hbm_budget")]
+
+
 _lib = None
 _dbl = C.POINTER(C.c_double)
 _i64 = C.POINTER(C.c_int64)
@@ -80,6 +86,14 @@ def lib():
         "sigw_debug_fail_alloc": (C.c_int, [C.c_int]),
         "sigw_plan_profile": (C.c_int, [P, C.c_int]),
         "sigw_fft3d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P]),
+        "sigw_generate_batch": (C.c_int, [P, C.POINTER(PZeta), C.POINTER(NGMap), C.POINTER(C.c_uint64), C.c_int, _i64]),
+        "sigw_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(Opts), C.POINTER(P)]),
+        "sigw_submit": (C.c_int, [P, C.c_int, C.c_double, C.POINTER(PZeta), C.POINTER(NGMap), C.c_uint64,
+                                  C.POINTER(C.c_uint64)]),
+        "sigw_poll": (C.c_int, [P, C.c_uint64, _dbl, _dbl]),
+        "sigw_wait": (C.c_int, [P, C.c_uint64, C.c_double, _dbl, _dbl]),
+        "sigw_server_stats_read": (C.c_int, [P, C.POINTER(ServerStats)]),
+        "sigw_server_destroy": (C.c_int, [P]),
         "sigw_plan_profile_read": (C.c_int, [P, C.POINTER(Profile)]),
     }
     for name, (res, args) in sig.items():
@@ -208,6 +222,18 @@ class Plan:
         self.batch = len(sd)
         return hits
 
+    def generate_batch(self, specs):
+        """sigw_generate_batch: one realisation per workloads.Spec (same N and L), own parameters each."""
+        n = len(specs)
+        pz = (PZeta * n)(*[PZeta(s.A, s.sigma, s.kstar) for s in specs])
+        mp = (NGMap * n)(*[NGMap(MAP_KINDS[s.kind], s.F_NL, s.G_NL, s.usr_floor) for s in specs])
+        sd = np.ascontiguousarray([s.seed for s in specs], dtype=np.uint64)
+        hits = np.zeros(n, dtype=np.int64)
+        _check(lib().sigw_generate_batch(self._h, pz, mp, _ptr(sd, C.c_uint64), n, _ptr(hits, C.c_int64)), self._h,
+               "sigw_generate_batch")
+        self.batch = n
+        return hits
+
     def generate_spec(self, spec, seeds=None):
         return self.generate(spec.A, spec.sigma, spec.kstar, spec.kind, spec.F_NL, spec.G_NL, spec.usr_floor,
                              seeds=(spec.seed,) if seeds is None else seeds)
@@ -252,3 +278,65 @@ class Plan:
 
     def synchronize(self):
         _check(lib().sigw_synchronize(self._h), self._h, "sigw_synchronize")
+
+
+class Server:
+    """Continuous-batching spectrum server (sigw_server_create / sigw_submit / sigw_poll / sigw_wait)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=2, opts=None, **over):
+        self.opts = opts or default_opts(**over)
+        h = C.c_void_p()
+        _check(lib().sigw_server_create(int(hbm_budget_bytes), max_slots, C.byref(self.opts), C.byref(h)), None,
+               "sigw_server_create")
+        self._h = h
+        self._N = {}
+
+    def submit(self, spec):
+        t = C.c_uint64()
+        _check(lib().sigw_submit(self._h, spec.N, spec.L, C.byref(PZeta(spec.A, spec.sigma, spec.kstar)),
+                                 C.byref(NGMap(MAP_KINDS[spec.kind], spec.F_NL, spec.G_NL, spec.usr_floor)),
+                                 spec.seed, C.byref(t)), None, "sigw_submit")
+        self._N[t.value] = spec.N
+        return t.value
+
+    def poll(self, ticket):
+        """None while not ready, else (omega, latency_s)."""
+        om = np.zeros(self._N.get(ticket, 8) // 2)
+        lat = C.c_double()
+        st = lib().sigw_poll(self._h, ticket, _ptr(om, C.c_double), C.byref(lat))
+        if st == ENOTREADY:
+            return None
+        self._N.pop(ticket, None)
+        _check(st, None, "sigw_poll")
+        return om, lat.value
+
+    def wait(self, ticket, timeout_s=600.0):
+        om = np.zeros(self._N.get(ticket, 8) // 2)
+        lat = C.c_double()
+        st = lib().sigw_wait(self._h, ticket, timeout_s, _ptr(om, C.c_double), C.byref(lat))
+        if st != ETIMEOUT:
+            self._N.pop(ticket, None)
+        _check(st, None, "sigw_wait")
+        return om, lat.value
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().sigw_server_stats_read(self._h, C.byref(s)), None, "sigw_server_stats_read")
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sigw_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

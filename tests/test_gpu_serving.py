@@ -1,0 +1,90 @@
+"""Serving and batched synthesis through the C ABI: every result is the same alone and in the mix.
+
+Tolerance: FP32 path, 1e-4 relative per shell bin (the stated FP32 bound).  Members of a batch that share
+kernels with the single call are compared more tightly.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_27231_gb300 import build, sigw
+    build.build()
+    sigw.lib()
+    return sigw
+
+
+def _spec(N, kind, seed, F=0.0, sigma=0.5):
+    return workloads.Spec(N=N, L=1.0, A=1e-2, sigma=sigma, kstar=(N // 8) * 2 * np.pi, kind=kind,
+                          F_NL=F, seed=seed)
+
+
+def _alone(lib, spec):
+    with lib.Plan(spec.N, spec.L, precision=32) as p:
+        p.generate_spec(spec)
+        return p.spectrum()["omega"][0]
+
+
+def test_generate_batch_matches_single_calls(lib):
+    specs = [_spec(32, "gauss", 11), _spec(32, "local", 12, F=3.0, sigma=0.7), _spec(32, "usr", 13, sigma=0.3)]
+    with lib.Plan(32, 1.0, precision=32, max_batch=3) as p:
+        p.generate_batch(specs)
+        mixed = p.spectrum()["omega"]
+    for i, s in enumerate(specs):
+        np.testing.assert_allclose(mixed[i], _alone(lib, s), rtol=1e-4)
+    # non-Gaussian members run the same kernels alone and in the batch
+    np.testing.assert_array_equal(mixed[1], _alone(lib, specs[1]))
+
+
+def test_server_results_equal_alone(lib):
+    specs = []
+    seed = 100
+    for N in (16, 32, 64):
+        for kind, F in (("gauss", 0.0), ("local", 2.0), ("usr", 0.0)):
+            specs.append(_spec(N, kind, seed, F=F))
+            seed += 1
+    with lib.Server(40e9, max_slots=3, max_batch=2, precision=32) as srv:
+        tickets = [srv.submit(s) for s in specs]
+        results = [srv.wait(t, timeout_s=300) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(specs) and st["failed"] == 0
+    assert st["batches"] <= len(specs)
+    for s, (om, lat) in zip(specs, results):
+        assert lat > 0
+        np.testing.assert_allclose(om, _alone(lib, s), rtol=1e-4)
+
+
+def test_server_admission_under_small_budget(lib):
+    fp64_budget = lib.footprint(64, lib.default_opts(max_batch=1)) * 1.2
+    with lib.Server(fp64_budget, max_slots=2, max_batch=1, precision=32) as srv:
+        specs = [_spec(64, "local", 200 + i, F=1.0) for i in range(3)] + [_spec(32, "gauss", 210)]
+        tickets = [srv.submit(s) for s in specs]
+        with pytest.raises(lib.SigwError) as e:
+            srv.submit(_spec(128, "gauss", 1))
+        assert e.value.status == lib.EBUSY
+        results = [srv.wait(t, timeout_s=300) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == 4
+    assert st["hbm_peak"] <= fp64_budget
+    for s, (om, _) in zip(specs, results):
+        np.testing.assert_allclose(om, _alone(lib, s), rtol=1e-4)
+
+
+def test_server_wait_timeout_then_result(lib):
+    with lib.Server(40e9, max_slots=1, precision=32) as srv:
+        t = srv.submit(_spec(128, "gauss", 7))
+        with pytest.raises(lib.SigwError) as e:
+            srv.wait(t, timeout_s=1e-4)
+        assert e.value.status == lib.ETIMEOUT
+        om, lat = srv.wait(t, timeout_s=300)
+        assert np.all(np.isfinite(om)) and lat > 0
+        with pytest.raises(lib.SigwError):
+            srv.poll(t)  # ticket consumed
