@@ -116,6 +116,14 @@ struct sigw_plan_s {
   unsigned long long* d_hits = nullptr;
   uint64_t* d_seeds = nullptr;
   int* d_err = nullptr;  // OR-ed by kernels whose bounded waits gave up
+  int* d_shells_all = nullptr;   // 1..N/2, for the all-shells call (no upload, so it can be captured)
+  double* d_Nk_all = nullptr;
+  // CUDA graph of the all-shells spectrum loop, per realisation count
+  cudaGraphExec_t graph = nullptr;
+  int graph_batch = 0;
+  bool graphs_ok = true;
+  long long graph_launches[SIGW_NKINDS] = {0};
+  double graph_bytes[SIGW_NKINDS] = {0};
   int generated = 0;
   std::string err;
   // accounting (see sigw_profile)
@@ -421,6 +429,8 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
   ALLOC(p->d_hits, mb * sizeof(unsigned long long));
   ALLOC(p->d_seeds, mb * sizeof(uint64_t));
   ALLOC(p->d_err, sizeof(int));
+  ALLOC(p->d_shells_all, H * sizeof(int));
+  ALLOC(p->d_Nk_all, H * sizeof(double));
 #undef ALLOC
   if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return bail(SIGW_ECUDA);
   // tables
@@ -449,6 +459,13 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
       return bail(SIGW_ECUDA);
   }
   p->Nk = count_shell_modes(N);
+  {
+    std::vector<int> sh(H);
+    for (int i = 0; i < H; ++i) sh[i] = i + 1;
+    if (cudaMemcpy(p->d_shells_all, sh.data(), sizeof(int) * H, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_Nk_all, p->Nk.data() + 1, sizeof(double) * H, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(SIGW_ECUDA);
+  }
   *out = p;
   return SIGW_OK;
 }
@@ -456,6 +473,7 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
 sigw_status sigw_plan_destroy(sigw_plan p) {
   if (!p) return SIGW_OK;
   if (p->st) cudaStreamSynchronize(p->st);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
   for (void* q : p->allocs) cudaFree(q);
   prof_reset(p);
   for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
@@ -580,34 +598,19 @@ sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* m
   return sigw_generate_batch(p, pzs.data(), ms.data(), seeds, batch, usr_hits);
 }
 
-sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, double* dev_out) {
-  if (!p) return SIGW_EINVAL;
-  if (!p->generated) return fail(p, SIGW_ESTATE, "sigw_spectrum before sigw_generate");
+// Queue the hot loop for the shells sh (device copies in d_sh / d_nk) writing [batch][ns][4] to out.
+static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, const int* d_sh, const double* d_nk,
+                                    double* out) {
   const int N = p->N, H = N / 2;
-  std::vector<int> sh;
-  if (shells) {
-    if (n_shells < 1 || n_shells > H) return fail(p, SIGW_EINVAL, "n_shells out of range");
-    sh.assign(shells, shells + n_shells);
-  } else {
-    for (int s = 1; s <= H; ++s) sh.push_back(s);
-  }
-  for (int s : sh)
-    if (s < 1 || s > H) return fail(p, SIGW_EINVAL, "shell index out of range");
   const int ns = (int)sh.size();
   const int batch = p->generated;
-  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
-  std::vector<double> nk(ns);
-  for (int i = 0; i < ns; ++i) nk[i] = p->Nk[sh[i]];
   cudaStream_t st = p->st;
-  CKP(p, cudaMemcpyAsync(p->d_shells, sh.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st), "upload shells");
-  CKP(p, cudaMemcpyAsync(p->d_Nk, nk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st), "upload Nk");
   const int n_alpha = p->opts.n_alpha, nm1 = p->opts.n_modes + 1;
   const size_t NN = (size_t)N * N;
   const size_t cel = p->celem();
   void* Ta = p->d_T;
   void* Tb = (char*)p->d_T + (size_t)batch * p->B * NN * H * cel;
   const long pbs = (long)ns * 2 * p->sz.maxblk;
-  p->h2d += sizeof(int) * ns + sizeof(double) * ns;
   const double fieldb = (double)batch * NN * H * cel;  // one packed complex field per realisation batch
   const double phib = (double)batch * NN * (H + 1) * cel;
   for (int si = 0; si < ns; ++si) {
@@ -636,9 +639,89 @@ sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, do
   }
   const sigw::LaunchShape shp = OPS(p, shape, N);
   RUN(p, 6, (double)batch * ns * 2 * p->sz.maxblk * 8, "bin finalise",
-      sigw::launch_fin(p->d_partial, pbs, p->sz.maxblk, ns, p->d_shells, p->d_Nk, N, p->L, shp.tc_f3,
-                       dev_out ? dev_out : p->d_out, batch, st));
+      sigw::launch_fin(p->d_partial, pbs, p->sz.maxblk, ns, d_sh, d_nk, N, p->L, shp.tc_f3, out, batch, st));
   return SIGW_OK;
+}
+
+// Capture the all-shells loop into a CUDA graph for the current realisation count (thread-local capture mode,
+// so CUDA calls of other threads are unaffected).  On any failure graphs stay off for this plan.
+static bool capture_all_shells(sigw_plan p, const std::vector<int>& sh) {
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  long long l0[SIGW_NKINDS];
+  double b0[SIGW_NKINDS];
+  std::memcpy(l0, p->launches, sizeof(l0));
+  std::memcpy(b0, p->kbytes, sizeof(b0));
+  if (cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  const sigw_status s = enqueue_spectrum(p, sh, p->d_shells_all, p->d_Nk_all, p->d_out);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->st, &g);
+  bool ok = (s == SIGW_OK && e == cudaSuccess && g);
+  if (ok) ok = cudaGraphInstantiate(&p->graph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  (void)cudaGetLastError();
+  for (int k = 0; k < SIGW_NKINDS; ++k) {  // what one replay launches; not counted until replayed
+    p->graph_launches[k] = p->launches[k] - l0[k];
+    p->graph_bytes[k] = p->kbytes[k] - b0[k];
+    p->launches[k] = l0[k];
+    p->kbytes[k] = b0[k];
+  }
+  if (!ok) {
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+    return false;
+  }
+  p->graph_batch = p->generated;
+  return true;
+}
+
+sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, double* dev_out) {
+  if (!p) return SIGW_EINVAL;
+  if (!p->generated) return fail(p, SIGW_ESTATE, "sigw_spectrum before sigw_generate");
+  const int N = p->N, H = N / 2;
+  std::vector<int> sh;
+  if (shells) {
+    if (n_shells < 1 || n_shells > H) return fail(p, SIGW_EINVAL, "n_shells out of range");
+    sh.assign(shells, shells + n_shells);
+  } else {
+    for (int s = 1; s <= H; ++s) sh.push_back(s);
+  }
+  for (int s : sh)
+    if (s < 1 || s > H) return fail(p, SIGW_EINVAL, "shell index out of range");
+  const int ns = (int)sh.size();
+  const int batch = p->generated;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  cudaStream_t st = p->st;
+  double* out = dev_out ? dev_out : p->d_out;
+  if (!shells) {
+    // all shells: replay a captured graph (per-kernel event timing needs the direct launches)
+    if (!p->prof_on && p->graphs_ok) {
+      if (!p->graph || p->graph_batch != batch) p->graphs_ok = capture_all_shells(p, sh);
+      if (p->graphs_ok) {
+        CKP(p, cudaGraphLaunch(p->graph, st), "graph launch");
+        for (int k = 0; k < SIGW_NKINDS; ++k) {
+          p->launches[k] += p->graph_launches[k];
+          p->kbytes[k] += p->graph_bytes[k];
+        }
+        if (dev_out)
+          CKP(p, cudaMemcpyAsync(dev_out, p->d_out, sizeof(double) * 4 * batch * ns, cudaMemcpyDeviceToDevice, st),
+              "copy results");
+        return SIGW_OK;
+      }
+    }
+    return enqueue_spectrum(p, sh, p->d_shells_all, p->d_Nk_all, out);
+  }
+  std::vector<double> nk(ns);
+  for (int i = 0; i < ns; ++i) nk[i] = p->Nk[sh[i]];
+  CKP(p, cudaMemcpyAsync(p->d_shells, sh.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st), "upload shells");
+  CKP(p, cudaMemcpyAsync(p->d_Nk, nk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st), "upload Nk");
+  p->h2d += sizeof(int) * ns + sizeof(double) * ns;
+  return enqueue_spectrum(p, sh, p->d_shells, p->d_Nk, out);
 }
 
 sigw_status sigw_spectrum(sigw_plan p, const int* shells, int n_shells, double* omega, double* PA, double* PB,

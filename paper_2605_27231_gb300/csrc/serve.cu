@@ -9,6 +9,8 @@
 // the plans already resident; idle plans are evicted least-recently-used to make room.  When the oldest queued
 // request cannot be admitted, later requests may only reuse idle plans (no new allocation), so the head of the
 // queue cannot starve.  A request whose plan alone exceeds the budget is refused at submission (SIGW_EBUSY).
+// Plans run on streams whose priority falls with the lattice size (smaller lattices first), so short requests
+// are not held behind the thread blocks of long ones when they share the device.
 // Latency of a request = completion time - submission time.
 #include <cuda_runtime.h>
 
@@ -46,6 +48,7 @@ struct Req {
 
 struct PoolPlan {
   sigw_plan plan = nullptr;
+  cudaStream_t stream = nullptr;  // created by the server with a priority by lattice size
   int N = 0;
   double L = 0;
   size_t bytes = 0;
@@ -86,15 +89,41 @@ PoolPlan* idle_plan(sigw_server_s* s, int N, double L) {
   return nullptr;
 }
 
+struct Doomed {
+  sigw_plan plan;
+  cudaStream_t stream;
+};
+
+void destroy_all(std::vector<Doomed>& v) {
+  for (Doomed& d : v) {
+    if (d.plan) sigw_plan_destroy(d.plan);
+    if (d.stream) cudaStreamDestroy(d.stream);
+  }
+  v.clear();
+}
+
+// Stream priority for a lattice size: the device's greatest priority for the smallest lattices.
+int priority_for(int N) {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  // numerically lower is higher priority; N <= 64 greatest, each doubling one step lower
+  int p = greatest;
+  for (int n = 64; n < N && p < least; n *= 2) ++p;
+  return p;
+}
+
 // Evict idle plans (least recently used first) until `need` more bytes fit.  Called with the lock held;
 // returns false if it cannot make room.
-bool make_room(sigw_server_s* s, size_t need, std::vector<sigw_plan>* to_destroy) {
+bool make_room(sigw_server_s* s, size_t need, std::vector<Doomed>* to_destroy) {
   while (s->in_use + need > s->budget) {
     PoolPlan* lru = nullptr;
     for (PoolPlan* p : s->pool)
       if (!p->busy && !p->creating && (!lru || p->last_use < lru->last_use)) lru = p;
     if (!lru) return false;
-    to_destroy->push_back(lru->plan);
+    to_destroy->push_back({lru->plan, lru->stream});
     s->in_use -= lru->bytes;
     s->pool.erase(std::find(s->pool.begin(), s->pool.end(), lru));
     delete lru;
@@ -126,7 +155,7 @@ void worker_main(sigw_server_s* s) {
     Req* head = nullptr;
     bool create = false;
     size_t need = 0;
-    std::vector<sigw_plan> destroy;
+    std::vector<Doomed> destroy;
     for (size_t qi = 0; qi < s->queue.size(); ++qi) {
       Req* r = s->queue[qi];
       if ((use = idle_plan(s, r->N, r->L))) {
@@ -145,7 +174,7 @@ void worker_main(sigw_server_s* s) {
     if (!head) {
       if (!destroy.empty()) {
         lk.unlock();
-        for (sigw_plan p : destroy) sigw_plan_destroy(p);
+        destroy_all(destroy);
         lk.lock();
       }
       s->cv.wait(lk);
@@ -175,17 +204,25 @@ void worker_main(sigw_server_s* s) {
     }
     s->n_batches++;
     lk.unlock();
-    for (sigw_plan p : destroy) sigw_plan_destroy(p);
+    destroy_all(destroy);
     sigw_status st = SIGW_OK;
     if (create) {
       sigw_plan np = nullptr;
-      st = sigw_plan_create(head->N, head->L, &s->opts, nullptr, &np);
+      cudaStream_t ps = nullptr;
+      if (cudaStreamCreateWithPriority(&ps, cudaStreamNonBlocking, priority_for(head->N)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ps = nullptr;
+        st = SIGW_ECUDA;
+      }
+      if (st == SIGW_OK) st = sigw_plan_create(head->N, head->L, &s->opts, ps, &np);
       lk.lock();
       use->creating = false;
       if (st == SIGW_OK) {
         use->plan = np;
+        use->stream = ps;
         s->n_plans_created++;
       } else {
+        if (ps) cudaStreamDestroy(ps);
         s->in_use -= use->bytes;
         s->pool.erase(std::find(s->pool.begin(), s->pool.end(), use));
         delete use;
@@ -325,6 +362,7 @@ sigw_status sigw_server_destroy(sigw_server s) {
   for (std::thread& t : s->workers) t.join();
   for (PoolPlan* p : s->pool) {
     if (p->plan) sigw_plan_destroy(p->plan);
+    if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
   }
   for (auto& kv : s->reqs) delete kv.second;

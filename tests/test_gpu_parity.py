@@ -201,3 +201,19 @@ def test_usr256_sampled_shell_fp32(lib, dec):
     got, _, ghits = _gpu(lib, spec, shells, 32)
     np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=1e-4)
     assert abs(int(ghits[0]) - hits) <= max(2, hits // 100)
+
+
+def test_graph_replay_equals_direct_launches(lib):
+    """The all-shells call runs as a captured CUDA graph; it must give the bits of direct launches (explicit
+    shell list), on first capture, on replay and after a batch-size change forces a new capture."""
+    spec = workloads.scaled(workloads.workload("local128"), 32)
+    H = spec.N // 2
+    with lib.Plan(spec.N, spec.L, precision=32, max_batch=2) as p:
+        p.generate_spec(spec, seeds=[3, 4])
+        direct = p.spectrum(np.arange(1, H + 1))["omega"]
+        g1 = p.spectrum()["omega"]
+        g2 = p.spectrum()["omega"]
+        p.generate_spec(spec, seeds=[3])
+        g3 = p.spectrum()["omega"]
+    assert np.array_equal(direct, g1) and np.array_equal(g1, g2)
+    assert np.array_equal(g3[0], direct[0])
