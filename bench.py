@@ -102,8 +102,9 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     spec = workloads.workload(args.workload)
     batch = args.batch
-    seeds = [spec.seed + 1000 * rank + i for i in range(batch)] if args.workload != "usr256" else \
-        [s + 1000 * rank for s in workloads.USR256_SEEDS][:batch]
+    from paper_2605_27231_gb300 import shard
+    base = list(workloads.USR256_SEEDS) if args.workload == "usr256" else [spec.seed + i for i in range(batch)]
+    seeds = shard.seeds_for_rank((base * batch)[:batch], rank, ws)
     stream = torch.cuda.Stream()
     plan = sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=32, max_batch=batch)
     n_sh = spec.N // 2
@@ -112,6 +113,9 @@ def run_ours(args):
     def step():
         plan.generate_spec(spec, seeds=seeds)
         plan.spectrum_async(dev_out.data_ptr())
+
+    plan.generate_spec(spec, seeds=seeds)
+    tuned = dict(zip(("alpha_batch", "strided_variant", "tune_ms"), plan.autotune()))
 
     for _ in range(args.warmup):
         step()
@@ -212,7 +216,7 @@ def run_ours(args):
                        "seeds_per_step": batch, "shells": n_sh, "n_alpha": 50, "n_modes": 200,
                        "l2": "inputs larger than L2 (%.1f GB device working set per step)" % (sigw.footprint(
                            spec.N, sigw.default_opts(max_batch=batch)) / 1e9),
-                       "parallelism": "replicas, seeds sharded across ranks"},
+                       "parallelism": "replicas, seeds sharded across ranks", "autotuned": tuned},
             "e2e": {"value": e2e_value, "unit": "spectra/s", "h2d_bytes_per_step": io["h2d_bytes"] / args.steps,
                     "d2h_bytes_per_step": io["d2h_bytes"] / args.steps},
             "gpu_launches": launches,

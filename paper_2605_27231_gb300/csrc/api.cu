@@ -4,6 +4,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,6 +42,22 @@ int auto_alpha_batch(const sigw_opts& o) {
   return std::min(o.n_alpha, 10);
 }
 
+// Largest terms-per-launch the first-pass output buffer holds (the autotuner's largest candidate).
+int max_alpha_batch(const sigw_opts& o) {
+  if (o.alpha_batch > 0) return std::min(o.alpha_batch, o.n_alpha);
+  return std::min(o.n_alpha, 16);
+}
+
+// Process-wide autotuning results: (N, precision, realisations, n_alpha) -> (terms per launch, variant).
+struct TuneKey {
+  int N, prec, batch, n_alpha;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(N, prec, batch, n_alpha) < std::tie(o.N, o.prec, o.batch, o.n_alpha);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
 // Sizes (bytes) of every device buffer of a plan.
 struct Sizes {
   size_t phi, T, W, synth, F, F2, partial, out, lut, tab, tw, amp, rows_sq;
@@ -53,7 +72,7 @@ Sizes sizes_of(int N, const sigw_opts& o) {
   const size_t H = N / 2, NH = H + 1, NN = (size_t)N * N;
   const size_t rel = o.precision == 64 ? 8 : 4, cel = 2 * rel;
   const size_t mb = (size_t)o.max_batch;
-  const int B = auto_alpha_batch(o);
+  const int B = max_alpha_batch(o);
   sigw::LaunchShape sh = o.precision == 64 ? sigw::OpsRT<double>::shape(N) : sigw::OpsRT<float>::shape(N);
   s.maxblk = sh.maxblk_f3;
   s.phi = mb * NN * NH * cel;
@@ -91,7 +110,9 @@ struct sigw_plan_s {
   bool own_stream = false;
   sigw::Decomposition dec;
   Sizes sz{};
-  int B = 1;
+  int B = 1;        // terms per first/second-pass launch
+  int variant = 0;  // radix variant of the strided inverse passes
+  bool tuned_from_table = false;
   size_t msq_max = 0;
   std::vector<double> Nk;  // per shell 1..N/2
   // device buffers
@@ -459,6 +480,15 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
       return bail(SIGW_ECUDA);
   }
   p->Nk = count_shell_modes(N);
+  if (o.alpha_batch == 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(TuneKey{N, o.precision, o.max_batch, o.n_alpha});
+    if (it != g_tune.end()) {
+      p->B = it->second.first;
+      p->variant = it->second.second;
+      p->tuned_from_table = true;
+    }
+  }
   {
     std::vector<int> sh(H);
     for (int i = 0; i < H; ++i) sh[i] = i + 1;
@@ -610,6 +640,7 @@ static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, con
   const size_t cel = p->celem();
   void* Ta = p->d_T;
   void* Tb = (char*)p->d_T + (size_t)batch * p->B * NN * H * cel;
+  const int var = p->variant;
   const long pbs = (long)ns * 2 * p->sz.maxblk;
   const double fieldb = (double)batch * NN * H * cel;  // one packed complex field per realisation batch
   const double phib = (double)batch * NN * (H + 1) * cel;
@@ -626,8 +657,9 @@ static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, con
       for (int a0 = 0; a0 < n_alpha; a0 += p->B) {
         const int nb = std::min(p->B, n_alpha - a0);
         RUN(p, 1, phib + 2.0 * nb * fieldb, "P1",
-            OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, st));
-        RUN(p, 2, 5.0 * nb * fieldb, "P2", OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, st));
+            OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, var, st));
+        RUN(p, 2, 5.0 * nb * fieldb, "P2",
+            OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, var, st));
       }
       RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
           OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, st));
@@ -778,6 +810,77 @@ sigw_status sigw_fft3d(sigw_plan p, int direction, const void* in_dev, void* out
     RUN(p, 0, 0, "inverse axis 1", OPS(p, pass, N, Y, 1, +1, 1, p->d_tw, st));
     RUN(p, 0, 0, "rows C2R", OPS(p, rows_c2r, N, Y, out_dev, 1, 1.0, nullptr, p->d_tw, st));
   }
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* out_variant, double* out_ms) {
+  if (!p) return SIGW_EINVAL;
+  if (!p->generated) return fail(p, SIGW_ESTATE, "sigw_plan_autotune needs a generated field");
+  const int N = p->N, H = N / 2;
+  if (n_c == 0) n_c = std::max(1, H / 2);
+  if (n_c < 1 || n_c > H) return fail(p, SIGW_EINVAL, "autotune shell out of range");
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  const int batch = p->generated, n_alpha = p->opts.n_alpha, nm1 = p->opts.n_modes + 1;
+  const size_t NN = (size_t)N * N, cel = p->celem();
+  const int16_t* lut = p->d_lut + (size_t)(n_c - 1) * (p->msq_max + 1);
+  const int bmax = max_alpha_batch(p->opts);
+  const int nvar = OPS(p, variants, N);
+  cudaStream_t st = p->st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CKP(p, cudaEventCreate(&e0), "event");
+  CKP(p, cudaEventCreate(&e1), "event");
+  double best = 1e300;
+  int bestB = p->B, bestV = p->variant;
+  const int cands[] = {4, 5, 8, 10, 16};
+  sigw_status status = SIGW_OK;
+  for (int v = 0; v < nvar && status == SIGW_OK; ++v) {
+    for (int B : cands) {
+      if (B > bmax) continue;
+      void* Ta = p->d_T;
+      void* Tb = (char*)p->d_T + (size_t)batch * B * NN * H * cel;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // first pass warms the variant; the second is timed
+        cudaEventRecord(e0, st);
+        for (int a0 = 0; a0 < n_alpha; a0 += B) {
+          const int nb = std::min(B, n_alpha - a0);
+          cudaError_t e = OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[0], nm1, a0, nb, batch, p->d_tw, v, st);
+          if (e == cudaSuccess) e = OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, v, st);
+          if (e != cudaSuccess) {
+            status = cuda_fail(p, e, "autotune launch");
+            break;
+          }
+        }
+        cudaEventRecord(e1, st);
+        if (status != SIGW_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          status = cuda_fail(p, cudaGetLastError(), "autotune timing");
+          break;
+        }
+      }
+      if (status != SIGW_OK) break;
+      if (ms < best) {
+        best = ms;
+        bestB = B;
+        bestV = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != SIGW_OK) return status;
+  p->B = bestB;
+  p->variant = bestV;
+  if (p->graph) {  // the captured loop used the old choice
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{N, p->opts.precision, p->opts.max_batch, n_alpha}] = {bestB, bestV};
+  }
+  if (out_alpha_batch) *out_alpha_batch = bestB;
+  if (out_variant) *out_variant = bestV;
+  if (out_ms) *out_ms = best;
   return SIGW_OK;
 }
 

@@ -75,6 +75,15 @@ template <typename T, int N> struct Shape {
   static constexpr int TC3 = TC3_1 * P3 < 32 ? 32 / P3 : TC3_1;  // whole warps (the partial sum uses shuffles)
 };
 
+// Alternative radix of the strided inverse passes (autotuner variant 1): FP32, N >= 128 only.
+template <typename T, int N> struct AltStrided {
+  static constexpr bool exists = sizeof(T) == 4 && N >= 128;
+  static constexpr int E = Shape<T, N>::ES == 16 ? 8 : 16;
+  static constexpr int P = N / E;
+  static constexpr int TC0 = 256 / P;
+  static constexpr int TC = TC0 > N / 2 ? N / 2 : TC0;
+};
+
 template <int P> struct RowSync { using type = SyncWarp; };
 template <> struct RowSync<64> { using type = SyncBlock; };
 template <> struct RowSync<128> { using type = SyncBlock; };
@@ -333,13 +342,12 @@ __global__ void k_reduce_mean(const double* __restrict__ part, int nblk, double*
 // P1: first inverse pass along axis 0 for a tile of TC packed columns at fixed k1.
 //   V_a(n) = phi_a(cell(|n|^2)) Phi~(n)          (column 0: V(k2=0) + i V(k2=H), each with its own cell)
 //   Ta_a = IDFT_0[V_a],  Tb_a = IDFT_0[i n0^D V_a]
-template <typename T, int N>
+template <typename T, int N, int E_ = Shape<T, N>::ES, int TC_ = Shape<T, N>::TC>
 __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>* __restrict__ Ta,
                                             cx<T>* __restrict__ Tb, const int16_t* __restrict__ lut,
                                             const T* __restrict__ phitab, int nm1, int alpha0, int nb,
                                             const cx<T>* __restrict__ tw) {
-  using SH = Shape<T, N>;
-  constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2, NH = H + 1;
+  constexpr int E = E_, P = N / E_, TC = TC_, H = N / 2, NH = H + 1;
   using Lay = ColLayout<T, N, TC, E>;
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(smraw) + Lay::SIZE;  // N values (column 0 only)
@@ -407,12 +415,11 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
 //   W[1] = IDFT_1[i n1^D Ta]     (G_1)
 //   W[2] = IDFT_1[Tb]            (G_0)
 // One value array is live at a time (the Ta tile is reloaded through L1 for the second transform).
-template <typename T, int N>
+template <typename T, int N, int E_ = Shape<T, N>::ES, int TC_ = Shape<T, N>::TC>
 __global__ void __launch_bounds__(256, 2) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
                                                cx<T>* __restrict__ W, int n_alpha, int alpha0, int nb,
                                                const cx<T>* __restrict__ tw) {
-  using SH = Shape<T, N>;
-  constexpr int E = SH::ES, P = SH::PS, TC = SH::TC, H = N / 2;
+  constexpr int E = E_, P = N / E_, TC = TC_, H = N / 2;
   using Lay = ColLayout<T, N, TC, E>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;

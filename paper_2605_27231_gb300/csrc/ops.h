@@ -39,12 +39,14 @@ struct OpsRT {
   static LaunchShape shape(int N);
 
   // ---- hot path
+  // variant: radix choice of the two strided inverse passes (0 default; 1 the alternative, where variants(N) == 2)
+  static int variants(int N);
   // first inverse pass (axis 0) with the filter phi_a(cell) and the i n_0 gradient factor
   static cudaError_t p1(int N, const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
-                        int alpha0, int nb, int batch, const void* tw, cudaStream_t st);
+                        int alpha0, int nb, int batch, const void* tw, int variant, cudaStream_t st);
   // second inverse pass (axis 1), three outputs per term
   static cudaError_t p2(int N, const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
-                        const void* tw, cudaStream_t st);
+                        const void* tw, int variant, cudaStream_t st);
   // last inverse pass (axis 2, C2R) + sum_a sigma_a g_i g_j + forward R2C along axis 2 keeping k2 <= n_c
   // err: device int, OR-ed with 1 when a bounded wait of the bulk-copy pipeline gives up
   static cudaError_t p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,

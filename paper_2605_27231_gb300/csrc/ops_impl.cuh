@@ -60,28 +60,47 @@ struct OpsT {
     return cudaGetLastError();
   }
   // ------------------------------------------------------------ hot path
+  template <int N, int E, int TC>
+  static cudaError_t p1_v(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
+                          int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
+    const size_t sm = col_bytes<N, TC, E>() + N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
+    auto k = k_p1<T, N, E, TC>;
+    SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
+    dim3 grid((N / 2) / TC, N, batch);
+    k<<<grid, TC * (N / E), sm, st>>>((const C*)phi, (C*)Ta, (C*)Tb, lut, (const T*)phitab, nm1, alpha0, nb,
+                                      (const C*)tw);
+    return cudaGetLastError();
+  }
   template <int N>
   static cudaError_t p1_n(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
-                          int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
+                          int alpha0, int nb, int batch, const void* tw, int variant, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = col_bytes<N, SH::TC, SH::ES>() + N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
-    auto k = k_p1<T, N>;
-    SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
-    dim3 grid((N / 2) / SH::TC, N, batch);
-    k<<<grid, SH::TC * SH::PS, sm, st>>>((const C*)phi, (C*)Ta, (C*)Tb, lut, (const T*)phitab, nm1, alpha0, nb,
-                                         (const C*)tw);
+    using AL = AltStrided<T, N>;
+    if constexpr (AL::exists) {
+      if (variant == 1)
+        return p1_v<N, AL::E, AL::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
+    }
+    return p1_v<N, SH::ES, SH::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
+  }
+  template <int N, int E, int TC>
+  static cudaError_t p2_v(const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
+                          const void* tw, cudaStream_t st) {
+    const size_t sm = col_bytes<N, TC, E>();
+    auto k = k_p2<T, N, E, TC>;
+    SIGW_CHECK_LAUNCH(allow_smem(k, sm));
+    dim3 grid((N / 2) / TC, N, batch * nb);
+    k<<<grid, TC * (N / E), sm, st>>>((const C*)Ta, (const C*)Tb, (C*)W, n_alpha, alpha0, nb, (const C*)tw);
     return cudaGetLastError();
   }
   template <int N>
   static cudaError_t p2_n(const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
-                          const void* tw, cudaStream_t st) {
+                          const void* tw, int variant, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = col_bytes<N, SH::TC, SH::ES>();
-    auto k = k_p2<T, N>;
-    SIGW_CHECK_LAUNCH(allow_smem(k, sm));
-    dim3 grid((N / 2) / SH::TC, N, batch * nb);
-    k<<<grid, SH::TC * SH::PS, sm, st>>>((const C*)Ta, (const C*)Tb, (C*)W, n_alpha, alpha0, nb, (const C*)tw);
-    return cudaGetLastError();
+    using AL = AltStrided<T, N>;
+    if constexpr (AL::exists) {
+      if (variant == 1) return p2_v<N, AL::E, AL::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
+    }
+    return p2_v<N, SH::ES, SH::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
   }
   template <int N>
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
@@ -218,6 +237,15 @@ int OpsRT<T>::rows_blocks(int N) {
   return 0;
 }
 template <typename T>
+int OpsRT<T>::variants(int N) {
+  switch (N) {
+    case 128: return AltStrided<T, 128>::exists ? 2 : 1;
+    case 256: return AltStrided<T, 256>::exists ? 2 : 1;
+    case 512: return AltStrided<T, 512>::exists ? 2 : 1;
+  }
+  return 1;
+}
+template <typename T>
 LaunchShape OpsRT<T>::shape(int N) {
   switch (N) {
     case 8: return OpsT<T>::template shape_n<8>();
@@ -231,13 +259,13 @@ LaunchShape OpsRT<T>::shape(int N) {
 }
 template <typename T>
 cudaError_t OpsRT<T>::p1(int N, const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
-                      int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template p1_n<NN>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st)));
+                      int alpha0, int nb, int batch, const void* tw, int variant, cudaStream_t st) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template p1_n<NN>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, variant, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::p2(int N, const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
-                      const void* tw, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template p2_n<NN>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st)));
+                      const void* tw, int variant, cudaStream_t st) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template p2_n<NN>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, variant, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,

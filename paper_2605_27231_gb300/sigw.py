@@ -85,6 +85,7 @@ def lib():
         "sigw_cell_table": (C.c_int, [C.POINTER(Opts), C.c_int, C.c_int, C.POINTER(C.c_int16)]),
         "sigw_debug_fail_alloc": (C.c_int, [C.c_int]),
         "sigw_plan_profile": (C.c_int, [P, C.c_int]),
+        "sigw_plan_autotune": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dbl]),
         "sigw_fft3d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P]),
         "sigw_generate_batch": (C.c_int, [P, C.POINTER(PZeta), C.POINTER(NGMap), C.POINTER(C.c_uint64), C.c_int, _i64]),
         "sigw_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(Opts), C.POINTER(P)]),
@@ -263,6 +264,13 @@ class Plan:
 
     def fft3d(self, direction, in_ptr, out_ptr):
         _check(lib().sigw_fft3d(self._h, direction, C.c_void_p(in_ptr), C.c_void_p(out_ptr)), self._h, "sigw_fft3d")
+
+    def autotune(self, n_c=0):
+        """sigw_plan_autotune: returns (terms per launch, radix variant, ms)."""
+        b, v, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(lib().sigw_plan_autotune(self._h, n_c, C.byref(b), C.byref(v), C.byref(ms)), self._h,
+               "sigw_plan_autotune")
+        return b.value, v.value, ms.value
 
     def profile(self, enable=True):
         _check(lib().sigw_plan_profile(self._h, 1 if enable else 0), self._h, "sigw_plan_profile")

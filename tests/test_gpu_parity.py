@@ -217,3 +217,23 @@ def test_graph_replay_equals_direct_launches(lib):
         g3 = p.spectrum()["omega"]
     assert np.array_equal(direct, g1) and np.array_equal(g1, g2)
     assert np.array_equal(g3[0], direct[0])
+
+
+def test_autotune_keeps_results_and_seeds_later_plans(lib, dec):
+    """The autotuner only regroups terms per launch and changes the strided radix: results stay within FP32
+    round-off of the untuned plan (and within 1e-4 of the oracle); a later plan starts from the tuned choice."""
+    spec = workloads.workload("local128")
+    shells = [16, 40]
+    with lib.Plan(spec.N, spec.L, precision=32) as p:
+        p.generate_spec(spec)
+        before = p.spectrum(shells)["omega"][0]
+        B, v, ms = p.autotune()
+        after = p.spectrum(shells)["omega"][0]
+    assert B in (4, 5, 8, 10, 16) and v in (0, 1) and ms > 0
+    np.testing.assert_allclose(after, before, rtol=2e-5)
+    ref, _, _ = _oracle(spec, dec, shells)
+    np.testing.assert_allclose(after, ref["omega"], rtol=1e-4)
+    with lib.Plan(spec.N, spec.L, precision=32) as q:
+        q.generate_spec(spec)
+        again = q.spectrum(shells)["omega"][0]
+    assert np.array_equal(again, after)
