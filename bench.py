@@ -115,7 +115,7 @@ def run_ours(args):
         plan.spectrum_async(dev_out.data_ptr())
 
     plan.generate_spec(spec, seeds=seeds)
-    tuned = dict(zip(("alpha_batch", "strided_variant", "tune_ms"), plan.autotune()))
+    tuned = dict(zip(("alpha_batch", "variant_bits", "tune_ms"), plan.autotune()))
 
     for _ in range(args.warmup):
         step()

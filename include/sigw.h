@@ -194,9 +194,11 @@ sigw_status sigw_server_destroy(sigw_server srv);
  * one target shell (n_c; 0 picks N/4) for every candidate choice: terms per launch in {4, 5, 8, 10, 16} (at most
  * n_alpha, and at most opts->alpha_batch when that is set) and, where two exist (FP32, N >= 128), both radix
  * variants of the strided passes.  Keeps the fastest in the plan and in a process-wide table keyed by
- * (N, precision, max_batch, n_alpha) from which later plans with alpha_batch = 0 start.  Outputs nullable:
- * chosen terms per launch, variant (0 default radix, 1 alternative) and its time in ms for both kernels
- * (m = s).  Waits for the stream.  Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */
+ * (N, precision, max_batch, n_alpha) from which later plans with alpha_batch = 0 start; then times both radix
+ * forms of the last inverse pass (FP32, N = 128 and 256) on the terms just produced.  Outputs nullable: chosen
+ * terms per launch, variant bits (1: alternative strided radix, 2: radix-16 last pass) and the time in ms of the
+ * chosen strided passes plus last pass for one kernel (m = s).  Waits for the stream.
+ * Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */
 sigw_status sigw_plan_autotune(sigw_plan plan, int n_c, int* out_alpha_batch, int* out_variant, double* out_ms);
 
 /* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter,

@@ -662,7 +662,7 @@ static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, con
             OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, var, st));
       }
       RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
-          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, st));
+          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, var, st));
       RUN(p, 4, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
           OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st));
       RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3",
@@ -865,11 +865,41 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
       }
     }
   }
+  // last inverse pass: radix variants on the W just produced by the best strided choice
+  int bestP3 = 0;
+  if (status == SIGW_OK && OPS(p, p3_variants, N) > 1) {
+    {
+      void* Ta = p->d_T;
+      void* Tb = (char*)p->d_T + (size_t)batch * bestB * NN * H * cel;
+      for (int a0 = 0; a0 < n_alpha && status == SIGW_OK; a0 += bestB) {
+        const int nb = std::min(bestB, n_alpha - a0);
+        cudaError_t e = OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[0], nm1, a0, nb, batch, p->d_tw, bestV, st);
+        if (e == cudaSuccess) e = OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, bestV, st);
+        if (e != cudaSuccess) status = cuda_fail(p, e, "autotune launch");
+      }
+    }
+    float t3[2] = {1e30f, 1e30f};
+    for (int v3 = 0; v3 < 2 && status == SIGW_OK; ++v3) {
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, st);
+        cudaError_t e = OPS(p, p3, N, p->d_work, p->d_sigma[0], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err,
+                            v3 ? 2 : 0, st);
+        cudaEventRecord(e1, st);
+        if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t3[v3], e0, e1) != cudaSuccess) {
+          status = cuda_fail(p, e != cudaSuccess ? e : cudaGetLastError(), "autotune last pass");
+          break;
+        }
+      }
+    }
+    if (status == SIGW_OK && t3[1] < t3[0]) bestP3 = 2;
+    if (status == SIGW_OK) best += std::min(t3[0], t3[1]);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != SIGW_OK) return status;
   p->B = bestB;
-  p->variant = bestV;
+  p->variant = bestV | bestP3;
   if (p->graph) {  // the captured loop used the old choice
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
@@ -879,7 +909,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
     g_tune[TuneKey{N, p->opts.precision, p->opts.max_batch, n_alpha}] = {bestB, bestV};
   }
   if (out_alpha_batch) *out_alpha_batch = bestB;
-  if (out_variant) *out_variant = bestV;
+  if (out_variant) *out_variant = bestV | bestP3;
   if (out_ms) *out_ms = best;
   return SIGW_OK;
 }

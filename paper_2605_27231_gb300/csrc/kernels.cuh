@@ -493,9 +493,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   }
 }
 
-template <typename T, int N> struct P3Cfg {
+template <typename T, int N, int E_ = ((N >= 16) ? 8 : 4)> struct P3Cfg {
   static constexpr int H = N / 2;
-  static constexpr int E = (N >= 16) ? 8 : 4;
+  static constexpr int E = E_;
   static constexpr int P = N / E;
   static constexpr int STAGES = 2;
   using Lay = RowLayout<T, N, true, 4>;  // single exchange buffer per row
@@ -510,6 +510,13 @@ template <typename T, int N> struct P3Cfg {
   static constexpr int STAGE_ELEMS = 6 * RPC * H;  // three fields of two terms
   static constexpr size_t SMEM = smem_for(RPC);
   static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+// Radix-16 alternative of the last inverse pass (autotuner variant bit 2): FP32, N = 128 and 256, where it needs
+// one shared-memory exchange per transform instead of two.
+template <typename T, int N> struct AltP3 {
+  static constexpr bool exists = sizeof(T) == 4 && (N == 128 || N == 256);
+  static constexpr int E = 16;
 };
 
 // 1-D Hermitian spectrum value at index k (0..N-1) of a packed row held in shared memory:
@@ -545,11 +552,13 @@ __device__ __forceinline__ cx<T> herm_grad(const cx<T>* row, int k) {
 // Term pair (a, a+1) uses three complex transforms: (g2^a + i g1^a), (g0^a + i g0^{a+1}), (g2^{a+1} + i g1^{a+1}).
 // The six packed rows of a term pair stream into a STAGES-deep shared-memory ring by cp.async.bulk,
 // issued STAGES-1 pairs ahead by thread 0.
-template <typename T, int N>
-__global__ void __launch_bounds__(P3Cfg<T, N>::THREADS, 1) k_p3(const cx<T>* __restrict__ W, const T* __restrict__ sigma,
-                                                             int n_alpha, cx<T>* __restrict__ F, int n_c,
-                                                             const cx<T>* __restrict__ tw, int* __restrict__ err) {
-  using CF = P3Cfg<T, N>;
+template <typename T, int N, int E_ = ((N >= 16) ? 8 : 4)>
+__global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>* __restrict__ W,
+                                                                   const T* __restrict__ sigma, int n_alpha,
+                                                                   cx<T>* __restrict__ F, int n_c,
+                                                                   const cx<T>* __restrict__ tw,
+                                                                   int* __restrict__ err) {
+  using CF = P3Cfg<T, N, E_>;
   constexpr int E = CF::E, P = CF::P, H = N / 2, RPC = CF::RPC, STAGES = CF::STAGES;
   using Sync = typename RowSync<P>::type;
   using Lay = typename CF::Lay;

@@ -77,7 +77,7 @@ struct OpsT {
     using SH = Shape<T, N>;
     using AL = AltStrided<T, N>;
     if constexpr (AL::exists) {
-      if (variant == 1)
+      if (variant & 1)
         return p1_v<N, AL::E, AL::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
     }
     return p1_v<N, SH::ES, SH::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
@@ -98,19 +98,27 @@ struct OpsT {
     using SH = Shape<T, N>;
     using AL = AltStrided<T, N>;
     if constexpr (AL::exists) {
-      if (variant == 1) return p2_v<N, AL::E, AL::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
+      if (variant & 1) return p2_v<N, AL::E, AL::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
     }
     return p2_v<N, SH::ES, SH::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
   }
-  template <int N>
-  static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
+  template <int N, int E>
+  static cudaError_t p3_v(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
                           int* err, cudaStream_t st) {
-    using CF = P3Cfg<T, N>;
-    auto k = k_p3<T, N>;
+    using CF = P3Cfg<T, N, E>;
+    auto k = k_p3<T, N, E>;
     SIGW_CHECK_LAUNCH(allow_smem(k, CF::SMEM));
     dim3 grid((N * N) / CF::RPC, batch);
     k<<<grid, CF::THREADS, CF::SMEM, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw, err);
     return cudaGetLastError();
+  }
+  template <int N>
+  static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
+                          int* err, int variant, cudaStream_t st) {
+    if constexpr (AltP3<T, N>::exists) {
+      if (variant & 2) return p3_v<N, AltP3<T, N>::E>(W, sigma, n_alpha, F, n_c, batch, tw, err, st);
+    }
+    return p3_v<N, ((N >= 16) ? 8 : 4)>(W, sigma, n_alpha, F, n_c, batch, tw, err, st);
   }
   static void n1_range(int N, int n_c, int* lo, int* nk1) {
     const int H = N / 2;
@@ -237,6 +245,12 @@ int OpsRT<T>::rows_blocks(int N) {
   return 0;
 }
 template <typename T>
+int OpsRT<T>::p3_variants(int N) {
+  if (N == 128) return AltP3<T, 128>::exists ? 2 : 1;
+  if (N == 256) return AltP3<T, 256>::exists ? 2 : 1;
+  return 1;
+}
+template <typename T>
 int OpsRT<T>::variants(int N) {
   switch (N) {
     case 128: return AltStrided<T, 128>::exists ? 2 : 1;
@@ -269,8 +283,8 @@ cudaError_t OpsRT<T>::p2(int N, const void* Ta, const void* Tb, void* W, int n_a
 }
 template <typename T>
 cudaError_t OpsRT<T>::p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
-                      const void* tw, int* err, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, err, st)));
+                      const void* tw, int* err, int variant, cudaStream_t st) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, err, variant, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st) {
