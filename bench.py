@@ -106,7 +106,7 @@ def run_ours(args):
     base = list(workloads.USR256_SEEDS) if args.workload == "usr256" else [spec.seed + i for i in range(batch)]
     seeds = shard.seeds_for_rank((base * batch)[:batch], rank, ws)
     stream = torch.cuda.Stream()
-    plan = sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=32, max_batch=batch)
+    plan = sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=32, max_batch=batch, n_alpha=args.n_alpha)
     n_sh = spec.N // 2
     dev_out = torch.empty(batch * n_sh * 4, dtype=torch.float64, device="cuda")
 
@@ -213,7 +213,7 @@ def run_ours(args):
             "dtype": "f32", "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
             "config": {"workload": args.workload, "N": spec.N, "L": spec.L, "A": spec.A, "sigma": spec.sigma,
                        "kstar_over_kf": round(spec.kstar * spec.L / (2 * 3.141592653589793), 6), "map": spec.kind,
-                       "seeds_per_step": batch, "shells": n_sh, "n_alpha": 50, "n_modes": 200,
+                       "seeds_per_step": batch, "shells": n_sh, "n_alpha": args.n_alpha, "n_modes": 200,
                        "l2": "inputs larger than L2 (%.1f GB device working set per step)" % (sigw.footprint(
                            spec.N, sigw.default_opts(max_batch=batch)) / 1e9),
                        "parallelism": "replicas, seeds sharded across ranks", "autotuned": tuned},
@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="usr256")
     ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--n-alpha", type=int, default=50, help="separable terms kept (the paper's 50; fewer only to "
+                    "shrink a profiling run)")
     ap.add_argument("--fp64-shells", type=int, default=4)
     ap.add_argument("--cpu-terms", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

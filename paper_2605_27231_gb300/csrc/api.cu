@@ -906,7 +906,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
   }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[TuneKey{N, p->opts.precision, p->opts.max_batch, n_alpha}] = {bestB, bestV};
+    g_tune[TuneKey{N, p->opts.precision, p->opts.max_batch, n_alpha}] = {bestB, bestV | bestP3};
   }
   if (out_alpha_batch) *out_alpha_batch = bestB;
   if (out_variant) *out_variant = bestV | bestP3;
