@@ -68,14 +68,18 @@ typedef struct sigw_pzeta {
 typedef enum sigw_mapkind {
   SIGW_MAP_GAUSS = 0, /* zeta = zeta_g (no FFT round trip) */
   SIGW_MAP_LOCAL = 1, /* zeta = zeta_g + F_NL (zeta_g^2 - <zeta_g^2>) + G_NL zeta_g^3, <.> the box mean */
-  SIGW_MAP_USR = 2    /* zeta = -1/3 ln(max(1 - 3 zeta_g, usr_floor)); hits below the floor are counted */
+  SIGW_MAP_USR = 2,   /* zeta = -1/3 ln(max(1 - 3 zeta_g, usr_floor)); hits below the floor are counted */
+  SIGW_MAP_NONLOCAL = 3 /* Eq. eq_nonlocal: zeta = zeta_g + alpha_NL / k*^2 lap(zeta_g^2) + beta_NL / k*^2 zeta_g
+                         * lap(zeta_g), k* the peak of P_zeta; lap is the spectral Laplacian -|k|^2 with
+                         * n_j = +N/2 on Nyquist indices (two extra FFT round trips) */
 } sigw_mapkind;
 
-/* F_NL is the coefficient of zeta_g^2 (F_NL = 3/5 f_NL). */
+/* F_NL is the coefficient of zeta_g^2 (F_NL = 3/5 f_NL); alpha_NL, beta_NL are used by SIGW_MAP_NONLOCAL only. */
 typedef struct sigw_ngmap {
   int kind;
   double F_NL, G_NL;
   double usr_floor; /* > 0; 1e-6 if 0 is given */
+  double alpha_NL, beta_NL;
 } sigw_ngmap;
 
 /* Plan options.  sigw_opts_default fills the paper's decomposition meta-parameters
@@ -138,6 +142,27 @@ sigw_status sigw_spectrum(sigw_plan plan, const int* shells, int n_shells, doubl
  * dev_out (device, [batch][n_shells][4] doubles: P_A, P_B, N_k, Omega).  n_shells <= N/2. */
 sigw_status sigw_spectrum_async(sigw_plan plan, const int* shells, int n_shells, double* dev_out);
 
+/* ---- The paper's per-target box (Sec. sec_numerical) ----
+ * The paper evaluates each target frequency k in its own box: L = pi N / k_max with k_max = 3 max(k, k_bar),
+ * where k_bar is the (1 - eps) quantile of the integral of Delta^2_zeta over ln k (eps = 0.1 in the paper).
+ * Reading used here (the paper is silent on placing k on the lattice): the target shell is
+ * n_c = round(k L / 2 pi) clamped to [1, N/2], and the box is then set to L = 2 pi n_c / k so that k_c = k exactly.
+ * For the log-normal of Eq. eq_lognormal, ln k_bar = ln k* + sigma sqrt(2) erfinv(1 - 2 eps).
+ * Host only.  Outputs: *L (box side), *n_c (target shell).  Errors: SIGW_EINVAL (N, k <= 0, eps not in (0, 1),
+ * bad P_zeta). */
+sigw_status sigw_target_box(int N, double k, const sigw_pzeta* pz, double eps, double* L, int* n_c);
+
+/* Changes the plan's box side to L > 0 (the lattice size N stays).  The next sigw_spectrum needs a new
+ * sigw_generate, since P_zeta on the lattice depends on L.  Errors: SIGW_EINVAL. */
+sigw_status sigw_plan_set_box(sigw_plan plan, double L);
+
+/* The paper's frequency scan: for each of n_k target wavenumbers k[i] (absolute, 1/length), its own box
+ * (sigw_target_box with eps), one realisation with the given seed, and Omega_GW at k[i] (the one shell n_c).
+ * Host outputs [n_k], any may be NULL: omega, L_out (box side used), nc_out (shell).  The plan's box is left at
+ * the last target's.  Same errors as sigw_generate / sigw_spectrum. */
+sigw_status sigw_target_scan(sigw_plan plan, const sigw_pzeta* pz, const sigw_ngmap* map, uint64_t seed,
+                             const double* k, int n_k, double eps, double* omega, double* L_out, int* nc_out);
+
 /* Copy Phi~ of realisation b to host memory in the standard half-spectrum layout
  * [k0][k1][k2], k2 = 0..N/2 (N*N*(N/2+1) complex values of the plan precision: float or double pairs),
  * continuum normalisation X~(k) = dx^3 sum_x X(x) e^{-ik.x}. */
@@ -196,7 +221,8 @@ sigw_status sigw_server_destroy(sigw_server srv);
  * variants of the strided passes.  Keeps the fastest in the plan and in a process-wide table keyed by
  * (N, precision, max_batch, n_alpha) from which later plans with alpha_batch = 0 start; then times both radix
  * forms of the last inverse pass (FP32, N = 128 and 256) on the terms just produced.  Outputs nullable: chosen
- * terms per launch, variant bits (1: alternative strided radix, 2: radix-16 last pass) and the time in ms of the
+ * terms per launch, variant bits (1: alternative radix of the first strided pass, 2: radix-16 last pass,
+ * 4: alternative radix of the second strided pass) and the time in ms of the
  * chosen strided passes plus last pass for one kernel (m = s).  Waits for the stream.
  * Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */
 sigw_status sigw_plan_autotune(sigw_plan plan, int n_c, int* out_alpha_batch, int* out_variant, double* out_ms);
@@ -223,6 +249,14 @@ sigw_status sigw_plan_profile_read(sigw_plan plan, sigw_profile* out);
  * (0: I_s, 1: I_c).  Same outputs as sigw_plan_kernel_terms; opts may be NULL (defaults).
  * Also reports all n_modes eigenvalues (sigma_all[n_modes], sorted by |sigma| descending) when non-NULL. */
 sigw_status sigw_decompose(const sigw_opts* opts, int m, double* sigma, double* phi, double* edges, double* sigma_all);
+
+/* Host-only decomposition study (the paper leaves the choice of grid meta-parameters open, Sec. sec_conclusions;
+ * Fig. fig_eigenvalues, Fig. fig_reconstruction).  For kernel m and the grid of opts, compares the rank-n_alpha
+ * truncation C_k = sum_{a < n_alpha} sigma_a q_a q_a^T with the full matrix C_ij = sqrt(L_i L_j) I_m(u_i, u_j)
+ * on the strip (Eq. eq_C_matrix_discrete).  Outputs (nullable): *frob = ||C - C_k||_F / ||C||_F,
+ * *maxrel = max_ij |C - C_k|_ij / max_ij |C_ij|, *gap = |sigma_{n_alpha}| / |sigma_{n_alpha - 1}| (0-based; the
+ * spectral gap at the cut, 0 when n_alpha = n_modes).  Errors: SIGW_EINVAL. */
+sigw_status sigw_decomposition_error(const sigw_opts* opts, int m, double* frob, double* maxrel, double* gap);
 
 /* Host-only: the cell table of target shell n_c, lut[msq] for msq = 0..msq_max: the u-grid cell holding
  * u = sqrt(msq)/n_c, decided on squares ((e_i n_c)^2 <= msq in FP64), or n_modes outside [umin, umax). */

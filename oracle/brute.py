@@ -21,11 +21,14 @@ from .sigw import polarisation_tensors, shell_modes
 from .synth import wavenumbers
 
 
-def omega_brute(Phi, L, dec, shells=None, kernel_matrices=None):
+def omega_brute(Phi, L, dec, shells=None, kernel_matrices=None, ball=False):
     """Omega_GW, P_A, P_B, N_k per shell by the direct sum.
 
     kernel_matrices : optional {m: K} with K_ij the kernel value on cells (i, j);
     defaults to dec.kernel_matrix(m, n_alpha) (the truncated separable kernel).
+    ball : sum only over the q1 with |n1| < u_max n_c.  The kernel vanishes once
+    |q1| / k_c leaves the u-grid (phi_a = 0 outside [u_min, u_max)), so the terms
+    dropped are exact zeros; this makes small shells of large lattices affordable.
     """
     N = Phi.shape[0]
     if shells is None:
@@ -33,11 +36,7 @@ def omega_brute(Phi, L, dec, shells=None, kernel_matrices=None):
     kf = 2.0 * np.pi / L
     V = L ** 3
     n = wavenumbers(N)
-    n0, n1, n2 = [a.ravel() for a in np.meshgrid(n, n, n, indexing="ij")]
-    msq = n0 ** 2 + n1 ** 2 + n2 ** 2
-    nD = np.stack([np.where(a == N // 2, 0, a) for a in (n0, n1, n2)], axis=1).astype(np.float64)
     Pf = Phi.ravel()
-    i0, i1, i2 = [a.ravel() for a in np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")]
     n_alpha = len(dec.sigma["s"])
     K = {}
     for m in ("s", "c"):
@@ -45,11 +44,30 @@ def omega_brute(Phi, L, dec, shells=None, kernel_matrices=None):
         Kp = np.zeros((Km.shape[0] + 1, Km.shape[1] + 1))
         Kp[:-1, :-1] = Km  # last row/column: the "outside the grid" cell, kernel 0
         K[m] = Kp
+    outside = K["s"].shape[0] - 1
+
+    def cells_at(n0, n1, n2, n_c):
+        c = cell_of(n0 * n0 + n1 * n1 + n2 * n2, n_c, dec.edges)
+        return np.where(c < 0, outside, c)
+
+    def deriv(n0, n1, n2):  # q_j / k_f with the Nyquist reading
+        return np.stack([np.where(a == N // 2, 0, a) for a in (n0, n1, n2)], axis=1).astype(np.float64)
+
     out = {"n_c": [], "omega": [], "PA": [], "PB": [], "Nk": []}
     for n_c in shells:
         kc = n_c * kf
-        cells = cell_of(msq, n_c, dec.edges)
-        cells = np.where(cells < 0, K["s"].shape[0] - 1, cells)
+        if ball:  # lattice wave numbers n1 (each axis in (-N/2, N/2]) with |n1| < u_max n_c
+            R = int(np.ceil(dec.edges[-1] * n_c))
+            r = n[(n >= -R) & (n <= R)]
+            a0, a1, a2 = [x.ravel() for x in np.meshgrid(r, r, r, indexing="ij")]
+            keep = a0 * a0 + a1 * a1 + a2 * a2 < (dec.edges[-1] * n_c) ** 2
+            a0, a1, a2 = a0[keep], a1[keep], a2[keep]
+        else:
+            a0, a1, a2 = [x.ravel() for x in np.meshgrid(n, n, n, indexing="ij")]
+        i0, i1, i2 = a0 % N, a1 % N, a2 % N  # array indices of q1
+        q1 = (i0 * N + i1) * N + i2
+        c1 = cells_at(a0, a1, a2, n_c)
+        d1 = deriv(a0, a1, a2)
         idx, nvec = shell_modes(N, n_c)
         ep, ex = polarisation_tensors(nvec)
         P = {"s": 0.0, "c": 0.0}
@@ -57,10 +75,13 @@ def omega_brute(Phi, L, dec, shells=None, kernel_matrices=None):
             k0, k1, k2 = idx[0][mode], idx[1][mode], idx[2][mode]
             j0, j1, j2 = (k0 - i0) % N, (k1 - i1) % N, (k2 - i2) % N
             q2 = (j0 * N + j1) * N + j2
-            base = Pf * Pf[q2]
+            b0, b1, b2 = n[j0], n[j1], n[j2]
+            c2 = cells_at(b0, b1, b2, n_c)
+            d2 = deriv(b0, b1, b2)
+            base = Pf[q1] * Pf[q2]
             for m, sign in (("s", +1.0), ("c", -1.0)):
-                w = K[m][cells, cells[q2]] * base
-                M = np.einsum("q,qi,qj->ij", w, nD, nD[q2])
+                w = K[m][c1, c2] * base
+                M = np.einsum("q,qi,qj->ij", w, d1, d2)
                 fac = sign * 4.0 * kf ** 2 / (kc ** 2 * V)
                 Ap = fac * np.sum(ep[mode] * M)
                 Ax = fac * np.sum(ex[mode] * M)

@@ -105,6 +105,17 @@ def build(n_modes=200, n_alpha=50, umin=1e-3, umax=15.0, upiv=1.0, sigp=0.5, Ap=
     return dec
 
 
+def truncation_error(dec, m, n_alpha):
+    """Rank-n_alpha truncation of C (Eq. eq_C_matrix_discrete) against C itself: (Frobenius relative error,
+    max-entry error relative to max |C|, |sigma_k| / |sigma_{k-1}| at the cut)."""
+    C = dec.C[m]
+    s, Q = dec.sigma_all[m][:n_alpha], dec.Q_all[m][:, :n_alpha]
+    D = C - (Q * s[None, :]) @ Q.T
+    w = dec.sigma_all[m]
+    gap = abs(w[n_alpha]) / abs(w[n_alpha - 1]) if n_alpha < len(w) and w[n_alpha - 1] != 0 else 0.0
+    return np.linalg.norm(D) / np.linalg.norm(C), np.abs(D).max() / np.abs(C).max(), gap
+
+
 def cell_of(msq, n_c, edges):
     """Cell index of lattice points with integer |n|^2 = msq for target shell n_c.
 

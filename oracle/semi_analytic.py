@@ -50,6 +50,20 @@ def omega_gauss(k, A, sigma, kstar):
     return integrate.quad(inner, 0.0, 1.0, limit=200, epsabs=0.0, epsrel=1e-9)[0]
 
 
+def k_bar(sigma, kstar, eps=0.1):
+    """(1 - eps) quantile of int Delta^2 dln k for the log-normal: a Gaussian CDF in ln k."""
+    from scipy.special import erfinv
+    return kstar * np.exp(sigma * np.sqrt(2.0) * erfinv(2.0 * (1.0 - eps) - 1.0))
+
+
+def target_box(N, k, A, sigma, kstar, eps=0.1):
+    """The paper's box for target k, placed on the lattice: n_c = round(k L / 2 pi) in [1, N/2] from the
+    rule's L, then L = 2 pi n_c / k so that k_c = k.  Returns (L, n_c)."""
+    L0 = box_size(N, k, A, sigma, kstar, eps)
+    n_c = int(min(N // 2, max(1, np.floor(k * L0 / (2.0 * np.pi) + 0.5))))
+    return 2.0 * np.pi * n_c / k, n_c
+
+
 def box_size(N, k, A, sigma, kstar, eps=0.1):
     """Paper's rule: L = pi N / k_max, k_max = 3 max(k, k_bar)."""
     # int_0^kbar Delta^2 dln k / int_0^inf = 1 - eps  -> for the log-normal, a Gaussian CDF in ln k

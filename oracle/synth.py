@@ -91,11 +91,29 @@ def apply_map(zg, kind, F_NL=0.0, G_NL=0.0, usr_floor=1e-6):
     raise ValueError(kind)
 
 
-def phi_tilde(N, L, A, sigma, kstar, seed, kind="gauss", F_NL=0.0, G_NL=0.0, usr_floor=1e-6):
+def laplacian(xt, L):
+    """Spectral Laplacian of a full-lattice spectrum: -k^2 X~ with k = k_f |n| (n_j = +-N/2 give the same k^2)."""
+    N = xt.shape[0]
+    n = wavenumbers(N)
+    n0, n1, n2 = np.meshgrid(n, n, n, indexing="ij")
+    return -((2.0 * np.pi / L) ** 2) * (n0 ** 2 + n1 ** 2 + n2 ** 2) * xt
+
+
+def nonlocal_map(zg, L, alpha_NL, beta_NL, kstar):
+    """Eq. eq_nonlocal: zeta = zeta_g + alpha_NL / k*^2 lap(zeta_g^2) + beta_NL / k*^2 zeta_g lap(zeta_g)."""
+    lap_zg2, _ = to_real(laplacian(to_fourier(zg * zg, L), L), L)
+    lap_zg, _ = to_real(laplacian(to_fourier(zg, L), L), L)
+    return zg + alpha_NL / kstar ** 2 * lap_zg2 + beta_NL / kstar ** 2 * zg * lap_zg
+
+
+def phi_tilde(N, L, A, sigma, kstar, seed, kind="gauss", F_NL=0.0, G_NL=0.0, usr_floor=1e-6, alpha_NL=0.0,
+              beta_NL=0.0):
     """Steps 1-4: full-lattice Phi~ (N^3 complex, FP64) and the USR floor-hit count."""
     zgt = zeta_g_tilde(N, L, A, sigma, kstar, seed)
     if kind == "gauss":
         return (2.0 / 3.0) * zgt, 0
     zg, _ = to_real(zgt, L)
+    if kind == "nonlocal":
+        return (2.0 / 3.0) * to_fourier(nonlocal_map(zg, L, alpha_NL, beta_NL, kstar), L), 0
     z, hits = apply_map(zg, kind, F_NL, G_NL, usr_floor)
     return (2.0 / 3.0) * to_fourier(z, L), hits

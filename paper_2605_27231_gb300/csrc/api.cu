@@ -78,7 +78,7 @@ Sizes sizes_of(int N, const sigw_opts& o) {
   s.phi = mb * NN * NH * cel;
   s.T = 2 * mb * (size_t)B * NN * H * cel;
   s.W = mb * 3 * (size_t)o.n_alpha * NN * H * cel;
-  s.synth = mb * (NN * H * cel + NN * NH * cel + NN * (size_t)N * rel) + 1024;
+  s.synth = mb * (NN * H * cel + NN * NH * cel + 3 * NN * (size_t)N * rel) + 1024;  // + two real fields (non-local map)
   s.F = mb * 6 * NN * NH * cel;
   s.F2 = mb * 6 * NN * NH * cel;
   s.partial = mb * H * 2 * (size_t)s.maxblk * sizeof(double);
@@ -369,6 +369,41 @@ sigw_status sigw_decompose(const sigw_opts* opts, int m, double* sigma, double* 
   return SIGW_OK;
 }
 
+sigw_status sigw_decomposition_error(const sigw_opts* opts, int m, double* frob, double* maxrel, double* gap) {
+  sigw_opts o;
+  if (opts) o = *opts; else sigw_opts_default(&o);
+  if (m < 0 || m > 1 || !valid_opts(o)) return SIGW_EINVAL;
+  sigw::DecompParams p = params_of(o);
+  const int n = p.n_modes, k = o.n_alpha;
+  p.n_alpha = n;  // every eigenpair
+  sigw::Decomposition d;
+  std::string e;
+  if (!sigw::build_decomposition(p, &d, &e)) return SIGW_EINVAL;
+  const sigw::KernelTerms& t = d.terms[m];
+  // q_a(i) = phi_a(i) sqrt(L_i); the full sum reproduces C, the first k terms give C_k
+  std::vector<double> q((size_t)n * n);
+  for (int a = 0; a < n; ++a)
+    for (int i = 0; i < n; ++i) q[(size_t)a * n + i] = t.phi[(size_t)a * n + i] * std::sqrt(d.widths[i]);
+  double num = 0.0, den = 0.0, dmax = 0.0, cmax = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double full = 0.0, part = 0.0;
+      for (int a = 0; a < n; ++a) {
+        const double v = t.sigma[a] * q[(size_t)a * n + i] * q[(size_t)a * n + j];
+        full += v;
+        if (a < k) part += v;
+      }
+      num += (full - part) * (full - part);
+      den += full * full;
+      dmax = std::max(dmax, std::fabs(full - part));
+      cmax = std::max(cmax, std::fabs(full));
+    }
+  if (frob) *frob = den > 0 ? std::sqrt(num / den) : 0.0;
+  if (maxrel) *maxrel = cmax > 0 ? dmax / cmax : 0.0;
+  if (gap) *gap = (k < n && t.sigma[k - 1] != 0.0) ? std::fabs(t.sigma[k]) / std::fabs(t.sigma[k - 1]) : 0.0;
+  return SIGW_OK;
+}
+
 sigw_status sigw_cell_table(const sigw_opts* opts, int n_c, int msq_max, int16_t* lut) {
   sigw_opts o;
   if (opts) o = *opts; else sigw_opts_default(&o);
@@ -536,12 +571,15 @@ sigw_status sigw_generate_batch(sigw_plan p, const sigw_pzeta* pz, const sigw_ng
   if (!p) return SIGW_EINVAL;
   if (!pz || !maps || !seeds || batch < 1 || batch > p->opts.max_batch)
     return fail(p, SIGW_EINVAL, "sigw_generate: bad arguments");
-  bool all_gauss = true, any_usr = false;
+  bool all_gauss = true, any_usr = false, any_nonlocal = false;
   for (int b = 0; b < batch; ++b) {
-    if (!(pz[b].A >= 0) || !(pz[b].sigma > 0) || !(pz[b].kstar > 0) || maps[b].kind < 0 || maps[b].kind > 2)
+    if (!(pz[b].A >= 0) || !(pz[b].sigma > 0) || !(pz[b].kstar > 0) || maps[b].kind < 0 || maps[b].kind > 3)
       return fail(p, SIGW_EINVAL, "sigw_generate: bad P_zeta or map parameters");
+    if (maps[b].kind == SIGW_MAP_NONLOCAL && !(std::isfinite(maps[b].alpha_NL) && std::isfinite(maps[b].beta_NL)))
+      return fail(p, SIGW_EINVAL, "sigw_generate: bad non-local map coefficients");
     all_gauss = all_gauss && maps[b].kind == SIGW_MAP_GAUSS;
     any_usr = any_usr || maps[b].kind == SIGW_MAP_USR;
+    any_nonlocal = any_nonlocal || maps[b].kind == SIGW_MAP_NONLOCAL;
   }
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
   const int N = p->N, H = N / 2;
@@ -560,8 +598,11 @@ sigw_status sigw_generate_batch(sigw_plan p, const sigw_pzeta* pz, const sigw_ng
       const double P = 2.0 * kPi * kPi * d2 / (k * k * k);
       amp[b * msq1 + msq] = std::sqrt(P * dx * dx * dx);
     }
-    margs[b] = sigw::MapArgs{maps[b].kind, maps[b].F_NL, maps[b].G_NL,
-                             maps[b].usr_floor > 0 ? maps[b].usr_floor : 1e-6};
+    const double ks2 = pz[b].kstar * pz[b].kstar;
+    margs[b] = maps[b].kind == SIGW_MAP_NONLOCAL
+                   ? sigw::MapArgs{maps[b].kind, maps[b].alpha_NL / ks2, maps[b].beta_NL / ks2, 1e-6}
+                   : sigw::MapArgs{maps[b].kind, maps[b].F_NL, maps[b].G_NL,
+                                   maps[b].usr_floor > 0 ? maps[b].usr_floor : 1e-6};
   }
   std::vector<unsigned char> buf;
   convert(amp, p->opts.precision, buf);
@@ -594,9 +635,28 @@ sigw_status sigw_generate_batch(sigw_plan p, const sigw_pzeta* pz, const sigw_ng
     const int rb = OPS(p, rows_blocks, N);
     RUN(p, 0, (double)batch * rb * 8, "mean zeta_g^2",
         sigw::launch_reduce_mean(p->d_sq, rb, p->d_mean, batch, 1.0 / ((double)NN * N), st));
+    void* R2 = nullptr;
+    void* R3 = nullptr;
+    if (any_nonlocal) {  // Eq. eq_nonlocal: lap(zeta_g) into R2 and lap(zeta_g^2) into R3
+      R2 = (char*)R + (size_t)p->opts.max_batch * NN * N * p->relem();
+      R3 = (char*)R2 + (size_t)p->opts.max_batch * NN * N * p->relem();
+      const double lap = kf * kf;
+      RUN(p, 0, Xb + Yb, "pack lap(zeta_g)", OPS(p, pack, N, X, Y, batch, st, lap));
+      RUN(p, 0, 2 * Yb, "inverse axis 0", OPS(p, pass, N, Y, 0, +1, batch, p->d_tw, st));
+      RUN(p, 0, 2 * Yb, "inverse axis 1", OPS(p, pass, N, Y, 1, +1, batch, p->d_tw, st));
+      RUN(p, 0, Yb + Rb, "rows C2R lap(zeta_g)", OPS(p, rows_c2r, N, Y, R2, batch, scale, nullptr, p->d_tw, st));
+      RUN(p, 0, Rb + Yb, "zeta_g^2 rows R2C", OPS(p, rows_r2c_square, N, R, Y, batch, p->d_tw, st));
+      RUN(p, 0, 2 * Yb, "forward axis 1", OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st));
+      RUN(p, 0, 2 * Yb, "forward axis 0", OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st));
+      RUN(p, 0, Yb + Xb, "unpack (zeta_g^2)", OPS(p, unpack, N, Y, X, batch, nullptr, 0L, dx * dx * dx, 1, st));
+      RUN(p, 0, Xb + Yb, "pack lap(zeta_g^2)", OPS(p, pack, N, X, Y, batch, st, lap));
+      RUN(p, 0, 2 * Yb, "inverse axis 0", OPS(p, pass, N, Y, 0, +1, batch, p->d_tw, st));
+      RUN(p, 0, 2 * Yb, "inverse axis 1", OPS(p, pass, N, Y, 1, +1, batch, p->d_tw, st));
+      RUN(p, 0, Yb + Rb, "rows C2R lap(zeta_g^2)", OPS(p, rows_c2r, N, Y, R3, batch, scale, nullptr, p->d_tw, st));
+    }
     CKP(p, cudaMemsetAsync(p->d_hits, 0, sizeof(unsigned long long) * batch, st), "memset hits");
-    RUN(p, 0, Rb + Yb, "map + rows R2C",
-        OPS(p, rows_r2c_map, N, R, Y, batch, p->d_maps, p->d_mean, p->d_hits, p->d_tw, st));
+    RUN(p, 0, Rb + Yb + (any_nonlocal ? 2 * Rb : 0.0), "map + rows R2C",
+        OPS(p, rows_r2c_map, N, R, Y, batch, p->d_maps, p->d_mean, p->d_hits, p->d_tw, st, R2, R3));
     RUN(p, 0, 2 * Yb, "forward axis 1", OPS(p, pass, N, Y, 1, -1, batch, p->d_tw, st));
     RUN(p, 0, 2 * Yb, "forward axis 0", OPS(p, pass, N, Y, 0, -1, batch, p->d_tw, st));
     RUN(p, 0, Yb + Xb, "unpack (Phi)",
@@ -830,39 +890,43 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
   CKP(p, cudaEventCreate(&e0), "event");
   CKP(p, cudaEventCreate(&e1), "event");
   double best = 1e300;
-  int bestB = p->B, bestV = p->variant;
+  int bestB = p->B, bestV = p->variant & 5;
   const int cands[] = {4, 5, 8, 10, 16};
   sigw_status status = SIGW_OK;
-  for (int v = 0; v < nvar && status == SIGW_OK; ++v) {
-    for (int B : cands) {
-      if (B > bmax) continue;
-      void* Ta = p->d_T;
-      void* Tb = (char*)p->d_T + (size_t)batch * B * NN * H * cel;
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {  // first pass warms the variant; the second is timed
-        cudaEventRecord(e0, st);
-        for (int a0 = 0; a0 < n_alpha; a0 += B) {
-          const int nb = std::min(B, n_alpha - a0);
-          cudaError_t e = OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[0], nm1, a0, nb, batch, p->d_tw, v, st);
-          if (e == cudaSuccess) e = OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, v, st);
-          if (e != cudaSuccess) {
-            status = cuda_fail(p, e, "autotune launch");
-            break;
-          }
-        }
-        cudaEventRecord(e1, st);
-        if (status != SIGW_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-          status = cuda_fail(p, cudaGetLastError(), "autotune timing");
-          break;
-        }
+  // For each terms-per-launch candidate the two strided passes are timed separately (each with both radix
+  // variants, bit 0 for the first pass and bit 2 for the second), so the best pair is found in 2 x nvar runs.
+  auto time_pass = [&](int which, int B, int v, float* ms) -> sigw_status {
+    void* Ta = p->d_T;
+    void* Tb = (char*)p->d_T + (size_t)batch * B * NN * H * cel;
+    for (int rep = 0; rep < 2; ++rep) {  // first pass warms the variant; the second is timed
+      cudaEventRecord(e0, st);
+      for (int a0 = 0; a0 < n_alpha; a0 += B) {
+        const int nb = std::min(B, n_alpha - a0);
+        cudaError_t e = which == 0
+                            ? OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[0], nm1, a0, nb, batch, p->d_tw, v, st)
+                            : OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, v << 2, st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "autotune launch");
       }
-      if (status != SIGW_OK) break;
-      if (ms < best) {
-        best = ms;
-        bestB = B;
-        bestV = v;
-      }
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+        return cuda_fail(p, cudaGetLastError(), "autotune timing");
+    }
+    return SIGW_OK;
+  };
+  for (int B : cands) {
+    if (B > bmax || status != SIGW_OK) continue;
+    float t1[2] = {1e30f, 1e30f}, t2[2] = {1e30f, 1e30f};
+    for (int v = 0; v < nvar && status == SIGW_OK; ++v) {
+      status = time_pass(0, B, v, &t1[v]);  // P1 writes the T that P2 reads next
+      if (status == SIGW_OK) status = time_pass(1, B, v, &t2[v]);
+    }
+    if (status != SIGW_OK) break;
+    const int v1 = t1[1] < t1[0] ? 1 : 0, v2 = t2[1] < t2[0] ? 1 : 0;
+    const double ms = (double)t1[v1] + (double)t2[v2];
+    if (ms < best) {
+      best = ms;
+      bestB = B;
+      bestV = v1 | (v2 << 2);
     }
   }
   // last inverse pass: radix variants on the W just produced by the best strided choice
@@ -911,6 +975,65 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
   if (out_alpha_batch) *out_alpha_batch = bestB;
   if (out_variant) *out_variant = bestV | bestP3;
   if (out_ms) *out_ms = best;
+  return SIGW_OK;
+}
+
+// ---- per-target box (Sec. sec_numerical)
+static double erfinv_bisect(double x) {  // erf(y) = x for x in (-1, 1), by bisection on the monotone erf
+  double lo = -7.0, hi = 7.0;
+  for (int i = 0; i < 200 && hi - lo > 1e-16; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    (std::erf(mid) < x ? lo : hi) = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+sigw_status sigw_target_box(int N, double k, const sigw_pzeta* pz, double eps, double* L, int* n_c) {
+  if (!pz || !L || !n_c || !is_pow2_in_range(N) || !(k > 0) || !(eps > 0 && eps < 1) || !(pz->kstar > 0) ||
+      !(pz->sigma > 0))
+    return SIGW_EINVAL;
+  const double kbar = pz->kstar * std::exp(pz->sigma * std::sqrt(2.0) * erfinv_bisect(1.0 - 2.0 * eps));
+  const double kmax = 3.0 * std::max(k, kbar);
+  const double Lrule = kPi * N / kmax;
+  long nc = std::lround(k * Lrule / (2.0 * kPi));
+  nc = std::max(1L, std::min((long)(N / 2), nc));
+  *n_c = (int)nc;
+  *L = 2.0 * kPi * (double)nc / k;
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_set_box(sigw_plan p, double L) {
+  if (!p) return SIGW_EINVAL;
+  if (!(L > 0) || !std::isfinite(L)) return fail(p, SIGW_EINVAL, "sigw_plan_set_box: L must be positive");
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  CKP(p, cudaStreamSynchronize(p->st), "set_box");
+  p->L = L;
+  p->generated = 0;
+  if (p->graph) {  // the captured finalisation holds the old L
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  return SIGW_OK;
+}
+
+sigw_status sigw_target_scan(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* map, uint64_t seed,
+                             const double* k, int n_k, double eps, double* omega, double* L_out, int* nc_out) {
+  if (!p) return SIGW_EINVAL;
+  if (!pz || !map || !k || n_k < 1) return fail(p, SIGW_EINVAL, "sigw_target_scan: bad arguments");
+  for (int i = 0; i < n_k; ++i) {
+    double L = 0.0;
+    int nc = 0;
+    if (sigw_target_box(p->N, k[i], pz, eps, &L, &nc) != SIGW_OK)
+      return fail(p, SIGW_EINVAL, "sigw_target_scan: bad target or P_zeta");
+    sigw_status s = sigw_plan_set_box(p, L);
+    if (s == SIGW_OK) s = sigw_generate(p, pz, map, &seed, 1, nullptr);
+    double om = 0.0;
+    if (s == SIGW_OK) s = sigw_spectrum(p, &nc, 1, &om, nullptr, nullptr, nullptr);
+    if (s != SIGW_OK) return s;
+    if (omega) omega[i] = om;
+    if (L_out) L_out[i] = L;
+    if (nc_out) nc_out[i] = nc;
+  }
   return SIGW_OK;
 }
 

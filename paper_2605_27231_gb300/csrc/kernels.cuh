@@ -91,12 +91,14 @@ template <> struct RowSync<128> { using type = SyncBlock; };
 // ================================================================ synthesis chain
 // Two real rows (2q, 2q+1) share one complex FFT: z = x1 + i x2, Z = DFT z,
 // X1(k) = (Z(k) + Z*(N-k))/2, X2(k) = -i/2 (Z(k) - Z*(N-k)).
-// MODE 0: rows from R;  MODE 1: Philox noise;  MODE 2: R through the NG map.
+// MODE 0: rows from R;  MODE 1: Philox noise;  MODE 2: R through the NG map;  MODE 3: R squared.
+// The non-local map (kind 3) also reads lap(zeta_g) from R2 and lap(zeta_g^2) from R3 (same layout as R).
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>* __restrict__ Y,
                                                   const cx<T>* __restrict__ tw, const uint64_t* __restrict__ seeds,
                                                   const MapArgs* __restrict__ maps, const double* __restrict__ mean,
-                                                  unsigned long long* __restrict__ hits) {
+                                                  unsigned long long* __restrict__ hits, const T* __restrict__ R2,
+                                                  const T* __restrict__ R3) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ER, P = SH::PR, H = N / 2;
   constexpr int PPC = SH::RPC;  // row pairs per CTA
@@ -127,9 +129,14 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>
         x1 = (T)gauss_draw((uint32_t)(row0 * N + x), sd);
         x2 = (T)gauss_draw((uint32_t)((row0 + 1) * N + x), sd);
       } else {
-        const T* rb = R + ((long)b * N * N + row0) * N;
+        const long ro = ((long)b * N * N + row0) * N;
+        const T* rb = R + ro;
         x1 = rb[x];
         x2 = rb[N + x];
+        if (MODE == 3) {
+          x1 = x1 * x1;
+          x2 = x2 * x2;
+        }
         if (MODE == 2) {
           T z[2] = {x1, x2};
 #pragma unroll
@@ -137,6 +144,9 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const T* __restrict__ R, cx<T>
             const T g = z[q];
             if (map.kind == 1) {
               z[q] = g + (T)map.F * (g * g - (T)mu) + (T)map.G * g * g * g;
+            } else if (map.kind == 3) {
+              const long o = ro + (long)q * N + x;
+              z[q] = g + (T)map.F * R3[o] + (T)map.G * g * R2[o];
             } else if (map.kind == 2) {
               T arg = (T)1 - (T)3 * g;
               if (arg < (T)map.floor) {
@@ -311,18 +321,29 @@ __global__ void k_unpack(const cx<T>* __restrict__ Y, cx<T>* __restrict__ X, int
   }
 }
 
+// Standard -> packed.  With lap != 0 each value is first multiplied by -lap |n|^2 (the spectral Laplacian for
+// lap = k_f^2; a Nyquist index counts as n = +N/2, which is exact for the second derivative).
 template <typename T>
-__global__ void k_pack(const cx<T>* __restrict__ X, cx<T>* __restrict__ Y, int N, long total) {
+__global__ void k_pack(const cx<T>* __restrict__ X, cx<T>* __restrict__ Y, int N, long total, double lap) {
   const int H = N / 2, NH = H + 1;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     const int c = (int)(i % H);
     const long q = i / H;
     const cx<T>* xr = X + q * NH;
+    T f0 = (T)1, fh = (T)1;
+    if (lap != 0.0) {
+      const int k1 = (int)(q % N), k0 = (int)((q / N) % N);
+      const int n0 = wrapn(k0, N), n1 = wrapn(k1, N);
+      const long m01 = (long)n0 * n0 + (long)n1 * n1;
+      f0 = (T)(-lap * (double)(m01 + (long)c * c));
+      fh = (T)(-lap * (double)(m01 + (long)H * H));
+    }
     if (c == 0) {
       const cx<T> x0 = xr[0], xh = xr[H];
-      Y[i] = mk<T>(x0.x - xh.y, x0.y + xh.x);  // X(0) + i X(H)
+      Y[i] = mk<T>(f0 * x0.x - fh * xh.y, f0 * x0.y + fh * xh.x);  // f0 X(0) + i fH X(H)
     } else {
-      Y[i] = xr[c];
+      const cx<T> v = xr[c];
+      Y[i] = mk<T>(f0 * v.x, f0 * v.y);
     }
   }
 }
@@ -381,32 +402,32 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
   const long fstride = (long)N * N * H;  // one field
   for (int a = 0; a < nb; ++a) {
     const T* tab = sm_tab + a * nm1;
-    cx<T> v[E];
+    // D = 0: V_a; D = 1: i n0 V_a.  V_a is formed again for the second transform instead of being kept,
+    // so only one value array is live next to the Phi~ tile.
+#pragma unroll 1
+    for (int D = 0; D < 2; ++D) {
+      cx<T> v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const T f = tab[cell[r]];
-      v[r] = mk<T>(f * ph[r].x, f * ph[r].y);
-      if (cc == 0) {
-        const int k0 = j + r * P;
-        const T fn = tab[sm_cn[k0]];
-        const cx<T> yn = sm_nyq[k0];
-        v[r] = mk<T>(v[r].x - fn * yn.y, v[r].y + fn * yn.x);
+      for (int r = 0; r < E; ++r) {
+        const T f = tab[cell[r]];
+        cx<T> x = mk<T>(f * ph[r].x, f * ph[r].y);
+        if (cc == 0) {
+          const int k0 = j + r * P;
+          const T fn = tab[sm_cn[k0]];
+          const cx<T> yn = sm_nyq[k0];
+          x = mk<T>(x.x - fn * yn.y, x.y + fn * yn.x);
+        }
+        if (D) {
+          const T nd = (T)derivn(j + r * P, N);
+          x = mk<T>(-nd * x.y, nd * x.x);
+        }
+        v[r] = x;
       }
+      fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
+      cx<T>* dst = (D ? Tb : Ta) + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
+#pragma unroll
+      for (int r = 0; r < E; ++r) dst[(long)(j + r * P) * N * H] = v[r];
     }
-    cx<T> w[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const T nd = (T)derivn(j + r * P, N);
-      w[r] = mk<T>(-nd * v[r].y, nd * v[r].x);  // i n0 v
-    }
-    fft_pencil<T, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
-    cx<T>* ta = Ta + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
-#pragma unroll
-    for (int r = 0; r < E; ++r) ta[(long)(j + r * P) * N * H] = v[r];
-    fft_pencil<T, N, E, +1, Lay, SyncBlock>(w, j, L, tw, SyncBlock());
-    cx<T>* tb = Tb + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
-#pragma unroll
-    for (int r = 0; r < E; ++r) tb[(long)(j + r * P) * N * H] = w[r];
   }
 }
 

@@ -15,7 +15,7 @@ struct LaunchShape {
 };
 
 struct MapArgs {
-  int kind;  // 0 gauss, 1 local, 2 usr
+  int kind;  // 0 gauss, 1 local, 2 usr, 3 non-local (F = alpha_NL / k*^2, G = beta_NL / k*^2)
   double F, G, floor;
 };
 
@@ -24,9 +24,12 @@ struct OpsRT {
   // ---- synthesis chain (packed layout [b][a0][a1][N/2], standard layout [b][k0][k1][N/2+1])
   static cudaError_t rows_r2c_noise(int N, void* Y, const uint64_t* seeds, int batch, const void* tw, cudaStream_t st);
   static cudaError_t rows_r2c_real(int N, const void* R, void* Y, int batch, const void* tw, cudaStream_t st);
-  // map: device array of per-realisation MapArgs
+  // map: device array of per-realisation MapArgs; R2 = lap(zeta_g), R3 = lap(zeta_g^2) for the non-local map
   static cudaError_t rows_r2c_map(int N, const void* R, void* Y, int batch, const MapArgs* map, const double* mean,
-                                  unsigned long long* hits, const void* tw, cudaStream_t st);
+                                  unsigned long long* hits, const void* tw, cudaStream_t st, const void* R2 = nullptr,
+                                  const void* R3 = nullptr);
+  // rows of R squared, R2C
+  static cudaError_t rows_r2c_square(int N, const void* R, void* Y, int batch, const void* tw, cudaStream_t st);
   static cudaError_t rows_c2r(int N, const void* Y, void* R, int batch, double scale, double* sq_partial,
                               const void* tw, cudaStream_t st);
   static cudaError_t pass(int N, void* Y, int axis, int dir, int batch, const void* tw, cudaStream_t st);
@@ -34,7 +37,8 @@ struct OpsRT {
   // mode 1: times factor
   static cudaError_t unpack(int N, const void* Y, void* X, int batch, const void* amp, long amp_bstride, double factor,
                             int mode, cudaStream_t st);
-  static cudaError_t pack(int N, const void* X, void* Y, int batch, cudaStream_t st);
+  // lap != 0: times -lap |n|^2 (spectral Laplacian for lap = k_f^2)
+  static cudaError_t pack(int N, const void* X, void* Y, int batch, cudaStream_t st, double lap = 0.0);
   static int rows_blocks(int N);  // CTAs per realisation of rows_c2r (entries of sq_partial per realisation)
   static LaunchShape shape(int N);
 

@@ -29,13 +29,15 @@ struct OpsT {
   // ------------------------------------------------------------ synthesis
   template <int N, int MODE>
   static cudaError_t rows_r2c_n(const void* R, void* Y, const uint64_t* seeds, const MapArgs* map, const double* mean,
-                                unsigned long long* hits, int batch, const void* tw, cudaStream_t st) {
+                                unsigned long long* hits, int batch, const void* tw, cudaStream_t st,
+                                const void* R2 = nullptr, const void* R3 = nullptr) {
     using SH = Shape<T, N>;
     const size_t sm = row_bytes<N>(SH::RPC);
     auto k = k_rows_r2c<T, N, MODE>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     dim3 grid((N * N / 2) / SH::RPC, batch);
-    k<<<grid, SH::RPC * SH::PR, sm, st>>>((const T*)R, (C*)Y, (const C*)tw, seeds, map, mean, hits);
+    k<<<grid, SH::RPC * SH::PR, sm, st>>>((const T*)R, (C*)Y, (const C*)tw, seeds, map, mean, hits, (const T*)R2,
+                                          (const T*)R3);
     return cudaGetLastError();
   }
   template <int N, bool SQ>
@@ -98,7 +100,7 @@ struct OpsT {
     using SH = Shape<T, N>;
     using AL = AltStrided<T, N>;
     if constexpr (AL::exists) {
-      if (variant & 1) return p2_v<N, AL::E, AL::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
+      if (variant & 4) return p2_v<N, AL::E, AL::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
     }
     return p2_v<N, SH::ES, SH::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
   }
@@ -188,8 +190,13 @@ cudaError_t OpsRT<T>::rows_r2c_real(int N, const void* R, void* Y, int batch, co
 }
 template <typename T>
 cudaError_t OpsRT<T>::rows_r2c_map(int N, const void* R, void* Y, int batch, const MapArgs* map, const double* mean,
-                                unsigned long long* hits, const void* tw, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 2>(R, Y, nullptr, map, mean, hits, batch, tw, st)));
+                                unsigned long long* hits, const void* tw, cudaStream_t st, const void* R2,
+                                const void* R3) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 2>(R, Y, nullptr, map, mean, hits, batch, tw, st, R2, R3)));
+}
+template <typename T>
+cudaError_t OpsRT<T>::rows_r2c_square(int N, const void* R, void* Y, int batch, const void* tw, cudaStream_t st) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template rows_r2c_n<NN, 3>(R, Y, nullptr, nullptr, nullptr, nullptr, batch, tw, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::rows_c2r(int N, const void* Y, void* R, int batch, double scale, double* sqp, const void* tw,
@@ -223,12 +230,12 @@ cudaError_t OpsRT<T>::unpack(int N, const void* Y, void* X, int batch, const voi
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t OpsRT<T>::pack(int N, const void* X, void* Y, int batch, cudaStream_t st) {
+cudaError_t OpsRT<T>::pack(int N, const void* X, void* Y, int batch, cudaStream_t st, double lap) {
   const long total = (long)batch * N * N * (N / 2);
   const int thr = 256;
   long blocks = (total + thr - 1) / thr;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  k_pack<T><<<(int)blocks, thr, 0, st>>>((const cx<T>*)X, (cx<T>*)Y, N, total);
+  k_pack<T><<<(int)blocks, thr, 0, st>>>((const cx<T>*)X, (cx<T>*)Y, N, total, lap);
   return cudaGetLastError();
 }
 template <typename T>

@@ -283,7 +283,7 @@ sigw_status sigw_server_create(size_t hbm_budget_bytes, int max_slots, const sig
 sigw_status sigw_submit(sigw_server s, int N, double L, const sigw_pzeta* pz, const sigw_ngmap* map, uint64_t seed,
                         uint64_t* ticket) {
   if (!s || !pz || !map || !ticket || !(L > 0) || N < 8 || N > 512 || (N & (N - 1))) return SIGW_EINVAL;
-  if (!(pz->A >= 0) || !(pz->sigma > 0) || !(pz->kstar > 0) || map->kind < 0 || map->kind > 2) return SIGW_EINVAL;
+  if (!(pz->A >= 0) || !(pz->sigma > 0) || !(pz->kstar > 0) || map->kind < 0 || map->kind > 3) return SIGW_EINVAL;
   const size_t need = footprint_of(s, N);
   std::lock_guard<std::mutex> lk(s->mu);
   if (need > s->budget) return SIGW_EBUSY;

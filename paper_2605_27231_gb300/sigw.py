@@ -13,8 +13,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsigw.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ETIMEOUT, EBUSY, ENOTREADY, ESTATE = range(9)
-MAP_GAUSS, MAP_LOCAL, MAP_USR = 0, 1, 2
-MAP_KINDS = {"gauss": MAP_GAUSS, "local": MAP_LOCAL, "usr": MAP_USR}
+MAP_GAUSS, MAP_LOCAL, MAP_USR, MAP_NONLOCAL = 0, 1, 2, 3
+MAP_KINDS = {"gauss": MAP_GAUSS, "local": MAP_LOCAL, "usr": MAP_USR, "nonlocal": MAP_NONLOCAL}
 
 
 class SigwError(RuntimeError):
@@ -34,7 +34,16 @@ class PZeta(C.Structure):
 
 
 class NGMap(C.Structure):
-    _fields_ = [("kind", C.c_int), ("F_NL", C.c_double), ("G_NL", C.c_double), ("usr_floor", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("F_NL", C.c_double), ("G_NL", C.c_double), ("usr_floor", C.c_double),
+                ("alpha_NL", C.c_double), ("beta_NL", C.c_double)]
+
+
+def _ngmap(kind, F_NL=0.0, G_NL=0.0, usr_floor=1e-6, alpha_NL=0.0, beta_NL=0.0):
+    return NGMap(MAP_KINDS[kind] if isinstance(kind, str) else kind, F_NL, G_NL, usr_floor, alpha_NL, beta_NL)
+
+
+def _spec_map(s):
+    return _ngmap(s.kind, s.F_NL, s.G_NL, s.usr_floor, getattr(s, "alpha_NL", 0.0), getattr(s, "beta_NL", 0.0))
 
 
 NKINDS = 7
@@ -96,6 +105,11 @@ def lib():
         "sigw_server_stats_read": (C.c_int, [P, C.POINTER(ServerStats)]),
         "sigw_server_destroy": (C.c_int, [P]),
         "sigw_plan_profile_read": (C.c_int, [P, C.POINTER(Profile)]),
+        "sigw_target_box": (C.c_int, [C.c_int, C.c_double, C.POINTER(PZeta), C.c_double, _dbl, C.POINTER(C.c_int)]),
+        "sigw_plan_set_box": (C.c_int, [P, C.c_double]),
+        "sigw_decomposition_error": (C.c_int, [C.POINTER(Opts), C.c_int, _dbl, _dbl, _dbl]),
+        "sigw_target_scan": (C.c_int, [P, C.POINTER(PZeta), C.POINTER(NGMap), C.c_uint64, _dbl, C.c_int, C.c_double,
+                                       _dbl, _dbl, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -144,6 +158,15 @@ def decompose(m, opts=None, all_sigma=False):
     return sigma, phi, edges, sall
 
 
+def decomposition_error(m, opts=None, **over):
+    """sigw_decomposition_error (host only): (frob, maxrel, gap) of the rank-n_alpha truncation of kernel m."""
+    o = opts or default_opts(**over)
+    f, mx, g = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().sigw_decomposition_error(C.byref(o), m, C.byref(f), C.byref(mx), C.byref(g)), None,
+           "sigw_decomposition_error")
+    return f.value, mx.value, g.value
+
+
 def cell_table(n_c, msq_max, opts=None):
     o = opts or default_opts()
     lut = np.zeros(msq_max + 1, dtype=np.int16)
@@ -162,6 +185,14 @@ def fft3d_noalloc(N, precision, direction, in_ptr, out_ptr, stream=None):
     """sigw_fft3d_noalloc: the 3-D real FFT with no plan and no device allocation (N <= 128 FP32, <= 64 FP64)."""
     _check(lib().sigw_fft3d_noalloc(N, precision, direction, C.c_void_p(in_ptr), C.c_void_p(out_ptr),
                                     C.c_void_p(stream) if stream else None), None, "sigw_fft3d_noalloc")
+
+
+def target_box(N, k, A, sigma, kstar, eps=0.1):
+    """sigw_target_box: the paper's per-target box; returns (L, n_c)."""
+    L, nc = C.c_double(), C.c_int()
+    pz = PZeta(A, sigma, kstar)
+    _check(lib().sigw_target_box(N, k, C.byref(pz), eps, C.byref(L), C.byref(nc)), None, "sigw_target_box")
+    return L.value, nc.value
 
 
 def debug_fail_alloc(n):
@@ -212,10 +243,11 @@ class Plan:
                                             _ptr(edges, C.c_double)), self._h, "kernel_terms")
         return sigma, phi, edges
 
-    def generate(self, A, sigma, kstar, kind="gauss", F_NL=0.0, G_NL=0.0, usr_floor=1e-6, seeds=(1,)):
+    def generate(self, A, sigma, kstar, kind="gauss", F_NL=0.0, G_NL=0.0, usr_floor=1e-6, seeds=(1,), alpha_NL=0.0,
+                 beta_NL=0.0):
         """sigw_generate; returns the USR floor-hit counts per realisation."""
         pz = PZeta(A, sigma, kstar)
-        mp = NGMap(MAP_KINDS[kind] if isinstance(kind, str) else kind, F_NL, G_NL, usr_floor)
+        mp = _ngmap(kind, F_NL, G_NL, usr_floor, alpha_NL, beta_NL)
         sd = np.ascontiguousarray(seeds, dtype=np.uint64)
         hits = np.zeros(len(sd), dtype=np.int64)
         _check(lib().sigw_generate(self._h, C.byref(pz), C.byref(mp), _ptr(sd, C.c_uint64), len(sd),
@@ -227,7 +259,7 @@ class Plan:
         """sigw_generate_batch: one realisation per workloads.Spec (same N and L), own parameters each."""
         n = len(specs)
         pz = (PZeta * n)(*[PZeta(s.A, s.sigma, s.kstar) for s in specs])
-        mp = (NGMap * n)(*[NGMap(MAP_KINDS[s.kind], s.F_NL, s.G_NL, s.usr_floor) for s in specs])
+        mp = (NGMap * n)(*[_spec_map(s) for s in specs])
         sd = np.ascontiguousarray([s.seed for s in specs], dtype=np.uint64)
         hits = np.zeros(n, dtype=np.int64)
         _check(lib().sigw_generate_batch(self._h, pz, mp, _ptr(sd, C.c_uint64), n, _ptr(hits, C.c_int64)), self._h,
@@ -237,7 +269,8 @@ class Plan:
 
     def generate_spec(self, spec, seeds=None):
         return self.generate(spec.A, spec.sigma, spec.kstar, spec.kind, spec.F_NL, spec.G_NL, spec.usr_floor,
-                             seeds=(spec.seed,) if seeds is None else seeds)
+                             seeds=(spec.seed,) if seeds is None else seeds, alpha_NL=getattr(spec, "alpha_NL", 0.0),
+                             beta_NL=getattr(spec, "beta_NL", 0.0))
 
     def spectrum(self, shells=None):
         """sigw_spectrum; dict of [batch, n_shells] arrays: omega, PA, PB, Nk (and n_c)."""
@@ -251,6 +284,24 @@ class Plan:
         out["Nk"] = nk
         out["n_c"] = sh
         return out
+
+    def set_box(self, L):
+        _check(lib().sigw_plan_set_box(self._h, L), self._h, "sigw_plan_set_box")
+        self.L = L
+
+    def target_scan(self, k, A, sigma, kstar, kind="gauss", F_NL=0.0, G_NL=0.0, usr_floor=1e-6, seed=1, eps=0.1):
+        """sigw_target_scan: Omega_GW at each target k in its own box; returns dict omega, L, n_c."""
+        kk = np.ascontiguousarray(k, dtype=np.float64)
+        n = len(kk)
+        pz = PZeta(A, sigma, kstar)
+        mp = _ngmap(kind, F_NL, G_NL, usr_floor)
+        om, Ls, nc = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32)
+        _check(lib().sigw_target_scan(self._h, C.byref(pz), C.byref(mp), seed, _ptr(kk, C.c_double), n, eps,
+                                      _ptr(om, C.c_double), _ptr(Ls, C.c_double), _ptr(nc, C.c_int)), self._h,
+               "sigw_target_scan")
+        self.L = float(Ls[-1])
+        self.batch = 1
+        return {"omega": om, "L": Ls, "n_c": nc}
 
     def spectrum_async(self, dev_out_ptr, shells=None):
         sh = np.arange(1, self.N // 2 + 1, dtype=np.int32) if shells is None else np.ascontiguousarray(shells, dtype=np.int32)
@@ -302,7 +353,7 @@ class Server:
     def submit(self, spec):
         t = C.c_uint64()
         _check(lib().sigw_submit(self._h, spec.N, spec.L, C.byref(PZeta(spec.A, spec.sigma, spec.kstar)),
-                                 C.byref(NGMap(MAP_KINDS[spec.kind], spec.F_NL, spec.G_NL, spec.usr_floor)),
+                                 C.byref(_spec_map(spec)),
                                  spec.seed, C.byref(t)), None, "sigw_submit")
         self._N[t.value] = spec.N
         return t.value

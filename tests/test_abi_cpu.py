@@ -88,3 +88,41 @@ def test_cell_table_matches_oracle(sigw):
         ref = odec.cell_of(msq, n_c, dec.edges)
         ref = np.where(ref < 0, 200, ref)
         np.testing.assert_array_equal(lut, ref)
+
+
+def test_target_box_matches_oracle(sigw):
+    """The per-target box rule (host only) against the oracle's own implementation."""
+    from oracle import semi_analytic
+    for N in (32, 64, 128, 256):
+        for sigma in (0.1, 0.5, 1.0):
+            for k in np.geomspace(0.05, 8.0, 23):
+                L, nc = sigw.target_box(N, k, 1e-2, sigma, 1.3)
+                Lo, nco = semi_analytic.target_box(N, k, 1e-2, sigma, 1.3)
+                assert nc == nco and abs(L / Lo - 1) < 1e-12
+    with pytest.raises(sigw.SigwError):
+        sigw.target_box(64, -1.0, 1e-2, 0.5, 1.0)
+    with pytest.raises(sigw.SigwError):
+        sigw.target_box(64, 1.0, 1e-2, 0.5, 1.0, eps=1.5)
+
+
+def test_decomposition_error_matches_oracle(sigw):
+    """The host decomposition study routine against the oracle's truncation error (independent eigen-solvers;
+    the truncated matrix is basis-independent when the cut is not degenerate)."""
+    for up, ap in ((1.0, 10.0), (0.8, 0.0)):
+        d = odec.build(n_modes=60, n_alpha=20, upiv=up, Ap=ap)
+        for m, mk in ((0, "s"), (1, "c")):
+            for k in (10, 20, 40):
+                f, mx, g = sigw.decomposition_error(m, n_modes=60, n_alpha=k, upiv=up, Ap=ap)
+                fo, mxo, go = odec.truncation_error(d, mk, k)
+                assert abs(f - fo) < 1e-9 and abs(mx - mxo) < 1e-9 and abs(g - go) < 1e-9
+
+
+def test_decomposition_sweep_and_optimal_choice(sigw):
+    from paper_2605_27231_gb300 import decomp_study
+    rows = decomp_study.sweep(0, n_modes=(60,), n_alpha=(10, 20, 30), upiv=(1.0,), Ap=(10.0,))
+    errs = [r["frob"] for r in sorted(rows, key=lambda r: r["n_alpha"])]
+    assert errs[0] >= errs[1] >= errs[2]
+    best = decomp_study.optimal(errs[1] * 1.0001, m=(0,), n_modes=(60,), n_alpha=(10, 20, 30), upiv=(1.0,),
+                                Ap=(10.0,))
+    assert best["n_alpha"] == 20
+    assert decomp_study.optimal(0.0, m=(0,), n_modes=(60,), n_alpha=(10,), upiv=(1.0,), Ap=(10.0,)) is None

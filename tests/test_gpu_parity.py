@@ -34,7 +34,7 @@ def dec():
 
 def _oracle(spec, dec, shells):
     Phi, hits = synth.phi_tilde(spec.N, spec.L, spec.A, spec.sigma, spec.kstar, spec.seed, spec.kind, spec.F_NL,
-                                spec.G_NL, spec.usr_floor)
+                                spec.G_NL, spec.usr_floor, spec.alpha_NL, spec.beta_NL)
     return osigw.omega(Phi, spec.L, dec, shells=shells), Phi, hits
 
 
@@ -99,6 +99,33 @@ def test_omega_all_shells_small(lib, dec, N, kind, F, precision):
     np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=RTOL[precision])
     np.testing.assert_allclose(got["PA"][0], ref["PA"], rtol=RTOL[precision])
     np.testing.assert_allclose(got["PB"][0], ref["PB"], rtol=RTOL[precision])
+
+
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_nonlocal_map_all_shells(lib, dec, N, precision):
+    """Eq. eq_nonlocal (alpha_NL = 5, beta_NL = -3 in units of 1/k*^2): Phi~ and every shell against the oracle."""
+    spec = workloads.Spec(N=N, L=1.0, A=2e-2, sigma=0.5, kstar=(N // 4) * 2 * np.pi, kind="nonlocal", seed=13,
+                          alpha_NL=5.0, beta_NL=-3.0)
+    ref, Phi, _ = _oracle(spec, dec, None)
+    got, phi, _ = _gpu(lib, spec, None, precision)
+    refh = Phi[:, :, :N // 2 + 1]
+    assert np.abs(phi - refh).max() <= (1e-12 if precision == 64 else 3e-6) * np.abs(refh).max()
+    np.testing.assert_array_equal(got["Nk"][0], ref["Nk"])
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=RTOL[precision])
+
+
+def test_mixed_batch_with_nonlocal_member(lib, dec):
+    """A batch mixing the non-local, local and Gaussian maps gives each member the spectrum it has alone."""
+    base = dict(N=16, L=1.0, A=2e-2, sigma=0.5, kstar=4 * 2 * np.pi)
+    specs = [workloads.Spec(kind="nonlocal", seed=1, alpha_NL=2.0, beta_NL=1.0, **base),
+             workloads.Spec(kind="local", F_NL=2.0, seed=2, **base), workloads.Spec(kind="gauss", seed=3, **base)]
+    with lib.Plan(16, 1.0, precision=64, max_batch=3) as p:
+        p.generate_batch(specs)
+        mixed = p.spectrum()["omega"]
+    for i, sp in enumerate(specs):
+        ref, _, _ = _oracle(sp, dec, None)
+        np.testing.assert_allclose(mixed[i], ref["omega"], rtol=1e-9)
 
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -203,6 +230,27 @@ def test_usr256_sampled_shell_fp32(lib, dec):
     assert abs(int(ghits[0]) - hits) <= max(2, hits // 100)
 
 
+@pytest.mark.slow
+def test_broad512_small_shells_fp32_fp64(lib, dec):
+    """The 512^3 local f_NL = -2 workload (A = 1e-2, sigma = 1, k* = 64 k_f), the largest lattice, on both paths.
+    The oracle side is the direct lattice sum over the kernel's support ball (|n1| < u_max n_c), which is
+    affordable for the first shells; Phi~ is compared element by element."""
+    from oracle import brute
+    spec = workloads.workload("broad512")
+    shells = [1, 2]
+    Phi, hits = synth.phi_tilde(spec.N, spec.L, spec.A, spec.sigma, spec.kstar, spec.seed, spec.kind, spec.F_NL,
+                                spec.G_NL, spec.usr_floor)
+    ref = brute.omega_brute(Phi, spec.L, dec, shells=shells, ball=True)
+    refh = Phi[:, :, :spec.N // 2 + 1]
+    for precision, rtol, ptol in ((32, 1e-4, 1e-5), (64, 1e-9, 1e-12)):
+        got, phi, _ = _gpu(lib, spec, shells, precision)
+        assert np.abs(phi - refh).max() <= ptol * np.abs(refh).max()
+        del phi
+        np.testing.assert_array_equal(got["Nk"][0], ref["Nk"])
+        np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=rtol)
+        np.testing.assert_allclose(got["PA"][0], ref["PA"], rtol=rtol)
+
+
 def test_graph_replay_equals_direct_launches(lib):
     """The all-shells call runs as a captured CUDA graph; it must give the bits of direct launches (explicit
     shell list), on first capture, on replay and after a batch-size change forces a new capture."""
@@ -229,7 +277,7 @@ def test_autotune_keeps_results_and_seeds_later_plans(lib, dec):
         before = p.spectrum(shells)["omega"][0]
         B, v, ms = p.autotune()
         after = p.spectrum(shells)["omega"][0]
-    assert B in (4, 5, 8, 10, 16) and v in (0, 1, 2, 3) and ms > 0
+    assert B in (4, 5, 8, 10, 16) and 0 <= v < 8 and ms > 0
     np.testing.assert_allclose(after, before, rtol=2e-5)
     ref, _, _ = _oracle(spec, dec, shells)
     np.testing.assert_allclose(after, ref["omega"], rtol=1e-4)

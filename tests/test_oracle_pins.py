@@ -242,6 +242,20 @@ def test_fft_route_equals_direct_sum_N16(dec):
     np.testing.assert_allclose(a["omega"], b["omega"], rtol=1e-11)
 
 
+def test_ball_restricted_direct_sum_equals_full_sum():
+    """Summing only over |n1| < u_max n_c drops exact zeros of the kernel: with u_max = 3 the ball is smaller
+    than the lattice for n_c <= 2 and covers it beyond; both forms agree in every shell to round-off."""
+    d3 = decomposition.build(n_modes=40, n_alpha=12, umax=3.0)
+    N, L = 16, 1.0
+    Phi, _ = synth.phi_tilde(N, L, 1e-2, 0.5, 3 * 2 * np.pi / L, seed=8, kind="local", F_NL=1.5)
+    a = brute.omega_brute(Phi, L, d3, shells=[1, 2, 3, 8])
+    b = brute.omega_brute(Phi, L, d3, shells=[1, 2, 3, 8], ball=True)
+    np.testing.assert_allclose(b["omega"], a["omega"], rtol=1e-12)
+    np.testing.assert_allclose(b["PB"], a["PB"], rtol=1e-12)
+    f = sigw.omega(Phi, L, d3, shells=[1, 2])
+    np.testing.assert_allclose(b["omega"][:2], f["omega"], rtol=1e-11)
+
+
 def test_full_rank_fft_route_equals_exact_kernel_sum(dec):
     """Keeping all N_modes eigenpairs, the FFT route equals the direct sum with the plain cell-centre
     kernel I(u_i, u_j) on the strip (no eigendecomposition on that side)."""
@@ -334,3 +348,69 @@ def test_wick_expectation_matches_semi_analytic(dec):
     w = wick.expected_omega(N, L, A, sig, kstar, dec, [n_c])["omega"][0]
     s = semi_analytic.omega_gauss(kstar, A, sig, kstar)
     assert abs(w / s - 1) < 0.10
+
+
+# ---------------------------------------------------------------- per-target box (Sec. sec_numerical)
+@pytest.mark.parametrize("sigma", [0.1, 0.5, 1.0])
+def test_k_bar_is_the_quantile_of_the_integrated_spectrum(sigma):
+    """k_bar encloses 1 - eps of int Delta^2 dln k: checked by quadrature, not through erfinv."""
+    A, kstar, eps = 1e-2, 2.0, 0.1
+    kb = semi_analytic.k_bar(sigma, kstar, eps)
+    f = lambda lk: synth.delta2_lognormal(np.exp(lk), A, sigma, kstar)
+    lo, hi = np.log(kstar) - 12 * sigma, np.log(kstar) + 12 * sigma
+    part = integrate.quad(f, lo, np.log(kb), epsabs=0, epsrel=1e-12)[0]
+    tot = integrate.quad(f, lo, hi, epsabs=0, epsrel=1e-12)[0]
+    assert abs(part / tot - (1 - eps)) < 1e-9
+
+
+def test_target_box_puts_k_on_a_shell_near_the_rule():
+    """k = n_c k_f exactly; the box differs from pi N / k_max only by the rounding of n_c."""
+    A, sigma, kstar = 1e-2, 0.5, 1.0
+    for N in (32, 64, 128):
+        for k in np.geomspace(0.05, 5.0, 37):
+            L, n_c = semi_analytic.target_box(N, k, A, sigma, kstar)
+            assert abs(n_c * 2 * np.pi / L - k) < 1e-12 * k
+            L0 = semi_analytic.box_size(N, k, A, sigma, kstar)
+            x = k * L0 / (2 * np.pi)  # the unrounded shell index
+            if 1 <= round(x) <= N // 2:
+                assert abs(n_c - x) <= 0.5 + 1e-12 and abs(L / L0 - 1) <= 0.5 / x + 1e-12
+            if k >= semi_analytic.k_bar(sigma, kstar):
+                assert abs(L0 - np.pi * N / (3 * k)) < 1e-12 * L0
+
+
+# ---------------------------------------------------------------- non-local map (Eq. eq_nonlocal)
+def test_nonlocal_map_on_a_plane_wave():
+    """For zeta_g = a cos(k.x): lap(zeta_g^2) = -2 k^2 a^2 cos(2 k.x) and zeta_g lap(zeta_g) = -k^2 a^2 cos^2(k.x)
+    (closed forms), so the map is known exactly."""
+    N, L, a, kstar, al, be = 16, 2.0, 0.3, 5.0, 1.7, -0.6
+    kf = 2 * np.pi / L
+    kv = kf * np.array([1.0, 2.0, 3.0])
+    x = np.arange(N) * L / N
+    X0, X1, X2 = np.meshgrid(x, x, x, indexing="ij")
+    ph = kv[0] * X0 + kv[1] * X1 + kv[2] * X2
+    k2 = kv @ kv
+    zg = a * np.cos(ph)
+    want = zg + al / kstar ** 2 * (-2 * k2 * a * a * np.cos(2 * ph)) + be / kstar ** 2 * (-k2 * a * a * np.cos(ph) ** 2)
+    got = synth.nonlocal_map(zg, L, al, be, kstar)
+    np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_nonlocal_map_with_zero_coefficients_is_the_identity():
+    a = synth.phi_tilde(16, 1.0, 1e-2, 0.5, 4 * 2 * np.pi, 3, "nonlocal", alpha_NL=0.0, beta_NL=0.0)[0]
+    b = synth.phi_tilde(16, 1.0, 1e-2, 0.5, 4 * 2 * np.pi, 3, "local", F_NL=0.0)[0]
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- decomposition study
+def test_truncation_error_is_the_eigenvalue_tail():
+    """For a symmetric matrix the Frobenius error of the rank-k eigen truncation is the root of the tail sum of
+    squared eigenvalues over the total (Eckart-Young); the oracle's matrix-based error must equal it."""
+    d = decomposition.build(n_modes=80, n_alpha=20)
+    for m in ("s", "c"):
+        w = d.sigma_all[m]
+        for k in (5, 20, 50):
+            f, mx, gap = decomposition.truncation_error(d, m, k)
+            assert abs(f - np.sqrt(np.sum(w[k:] ** 2) / np.sum(w ** 2))) < 1e-12
+            assert 0 < mx <= 1 and 0 < gap <= 1
+        errs = [decomposition.truncation_error(d, m, k)[0] for k in range(1, 80)]
+        assert np.all(np.diff(errs) <= 1e-15)

@@ -30,11 +30,13 @@ class Spec:
     A: float
     sigma: float
     kstar: float          # absolute wave number (1 / length)
-    kind: str             # "gauss" | "local" | "usr"
+    kind: str             # "gauss" | "local" | "usr" | "nonlocal"
     F_NL: float = 0.0     # local map coefficient (F_NL = 3/5 f_NL)
     G_NL: float = 0.0
     usr_floor: float = 1e-6
     seed: int = 1
+    alpha_NL: float = 0.0  # non-local map coefficients (Eq. eq_nonlocal), in units of 1 / k*^2
+    beta_NL: float = 0.0
 
     def as_dict(self):
         return asdict(self)
