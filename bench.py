@@ -231,6 +231,7 @@ def run_ours(args):
     if rank == 0 and args.serve_requests > 0:
         serving = serving_run(args)
     scan = paper_scan() if rank == 0 and not args.no_paper_scan else None
+    fftx = fft_crosscheck() if rank == 0 and not args.no_paper_scan else None
 
     if rank == 0:
         line = {
@@ -258,6 +259,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "serving": serving,
             "paper_workload_scan": scan,
+            "fft_crosscheck_cufft": fftx,
             "omega_finite_positive": omega_ok,
         }
         print(json.dumps(line))
@@ -311,6 +313,40 @@ def serving_run(args):
             "hbm_peak_gb": st["hbm_peak"] / 1e9, "budget_gb": args.serve_budget_gb,
             "mix": "N uniform over {64,128,256}; f_NL ~ U[-5,20]; sigma ~ U[0.1,1]; map uniform over "
                    "{gauss, local, usr}; Poisson arrivals, seed 7; FP32"}
+
+
+def fft_crosscheck(N=256, reps=10):
+    """The library's 3-D real FFT (sigw_fft3d: rows R2C + two strided passes + unpack) timed beside cuFFT
+    (torch.fft.rfftn, a library call) on the same N^3 input, FP32 and FP64, with the largest difference."""
+    import torch
+    from paper_2605_27231_gb300 import sigw
+    out = {}
+    for prec, rdt, cdt in ((32, torch.float32, torch.complex64), (64, torch.float64, torch.complex128)):
+        st = torch.cuda.Stream()
+        with sigw.Plan(N, 1.0, precision=prec, n_alpha=2, stream=st.cuda_stream) as p, torch.cuda.stream(st):
+            g = torch.Generator(device="cuda").manual_seed(5)
+            x = torch.randn((N, N, N), dtype=rdt, device="cuda", generator=g)
+            X = torch.empty((N, N, N // 2 + 1), dtype=cdt, device="cuda")
+            res = {}
+            for name, fn in (("ours", lambda: p.fft3d(-1, x.data_ptr(), X.data_ptr())),
+                             ("cufft", lambda: torch.fft.rfftn(x))):
+                for _ in range(3):
+                    fn()
+                st.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                for _ in range(reps):
+                    fn()
+                b.record(st)
+                b.synchronize()
+                res[name] = a.elapsed_time(b) / reps
+            p.fft3d(-1, x.data_ptr(), X.data_ptr())
+            ref = torch.fft.rfftn(x)
+            st.synchronize()
+            diff = float((X - ref).abs().max() / ref.abs().max())
+        out["fp%d" % prec] = {"ours_ms": res["ours"], "cufft_ms": res["cufft"], "max_abs_diff_over_max": diff}
+    out["transform"] = "%d^3 real -> half complex, one realisation" % N
+    return out
 
 
 def paper_scan(steps=3):

@@ -138,6 +138,17 @@ sigw_status sigw_generate_batch(sigw_plan plan, const sigw_pzeta* pz, const sigw
 sigw_status sigw_spectrum(sigw_plan plan, const int* shells, int n_shells, double* omega, double* PA, double* PB,
                           int64_t* Nk);
 
+/* Jackknife error bars (Sec. sec_envelope_obs): as sigw_spectrum, and for every shell the TT fields A_l, B_l on
+ * the shell modes are transformed to real space, the box is split into M^3 equal sub-volumes (M = 4 in the
+ * paper; N must be a multiple of M), and M^3 leave-one-out estimates P^(i) = (E - E_i) / ((1 - M^-3) V N_k) are
+ * formed from the real-space energies (E_i: sub-volume i, E: total).  sigma^2 = (M^3 - 1)/M^3 sum_i
+ * (P^(i) - P_bar)^2 for P_A, P_B and Omega.  The replica means equal the plain shell estimates (Parseval).
+ * shells: 1..N/2-1 (the Nyquist shell is not offered), NULL for all of them.  Host outputs [batch][n_shells], any
+ * may be NULL.  Allocates a partials buffer for the call (2 x 2 batch x M^3 x N/M doubles per shell).
+ * Errors: SIGW_ESTATE, SIGW_EINVAL, SIGW_ENOMEM, SIGW_ECUDA. */
+sigw_status sigw_spectrum_jackknife(sigw_plan plan, const int* shells, int n_shells, int M, double* omega,
+                                    double* sigma_omega, double* PA, double* sigma_PA, double* PB, double* sigma_PB);
+
 /* As sigw_spectrum, but only queues the work on the plan's stream and writes device memory:
  * dev_out (device, [batch][n_shells][4] doubles: P_A, P_B, N_k, Omega).  n_shells <= N/2. */
 sigw_status sigw_spectrum_async(sigw_plan plan, const int* shells, int n_shells, double* dev_out);

@@ -78,6 +78,8 @@ Sizes sizes_of(int N, const sigw_opts& o) {
   s.phi = mb * NN * NH * cel;
   s.T = 2 * mb * (size_t)B * NN * H * cel;
   s.W = mb * 3 * (size_t)o.n_alpha * NN * H * cel;
+  // the jackknife reuses W after each shell: two standard + two packed half spectra + two real fields
+  s.W = std::max(s.W, mb * 2 * (NN * NH * cel + NN * H * cel + NN * (size_t)N * rel) + 1024);
   s.synth = mb * (NN * H * cel + NN * NH * cel + 3 * NN * (size_t)N * rel) + 1024;  // + two real fields (non-local map)
   s.F = mb * 6 * NN * NH * cel;
   s.F2 = mb * 6 * NN * NH * cel;
@@ -688,9 +690,20 @@ sigw_status sigw_generate(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap* m
   return sigw_generate_batch(p, pzs.data(), ms.data(), seeds, batch, usr_hits);
 }
 
+// Jackknife scratch of one spectrum call (Sec. sec_envelope_obs): M^3 sub-volumes; per (shell, kernel) the TT
+// amplitudes go to Xj (standard half spectra, 2 per realisation), are packed into Yj, inverse-transformed into
+// the real fields Rj, and reduced per sub-volume x0-plane into part[(si * 2 + m)][2 batch][M^3][N/M].
+struct Jackknife {
+  int M = 4;
+  double* part = nullptr;
+  void* Xj = nullptr;
+  void* Yj = nullptr;
+  void* Rj = nullptr;
+};
+
 // Queue the hot loop for the shells sh (device copies in d_sh / d_nk) writing [batch][ns][4] to out.
 static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, const int* d_sh, const double* d_nk,
-                                    double* out) {
+                                    double* out, const Jackknife* jk = nullptr) {
   const int N = p->N, H = N / 2;
   const int ns = (int)sh.size();
   const int batch = p->generated;
@@ -725,8 +738,25 @@ static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, con
           OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, var, st));
       RUN(p, 4, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
           OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st));
-      RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3",
-          OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st));
+      if (!jk) {
+        RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3",
+            OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st));
+      } else {
+        const double xjb = 2.0 * batch * NN * (H + 1) * cel, yjb = 2.0 * batch * NN * H * cel;
+        const double rjb = 2.0 * batch * NN * N * p->relem();
+        CKP(p, cudaMemsetAsync(jk->Xj, 0, (size_t)xjb, st), "jackknife zero");
+        RUN(p, 5, 6.0 * batch * (double)N * disk * cel, "F3 + amplitudes",
+            OPS(p, f3, N, p->d_F2, n_c, p->d_partial + ((long)si * 2 + m) * p->sz.maxblk, pbs, batch, p->d_tw, st,
+                jk->Xj));
+        RUN(p, 0, xjb + yjb, "jackknife pack", OPS(p, pack, N, jk->Xj, jk->Yj, 2 * batch, st));
+        RUN(p, 0, 2 * yjb, "jackknife inverse axis 0", OPS(p, pass, N, jk->Yj, 0, +1, 2 * batch, p->d_tw, st));
+        RUN(p, 0, 2 * yjb, "jackknife inverse axis 1", OPS(p, pass, N, jk->Yj, 1, +1, 2 * batch, p->d_tw, st));
+        RUN(p, 0, yjb + rjb, "jackknife rows C2R",
+            OPS(p, rows_c2r, N, jk->Yj, jk->Rj, 2 * batch, 1.0, nullptr, p->d_tw, st));
+        const long per = 2L * batch * jk->M * jk->M * jk->M * (N / jk->M);
+        RUN(p, 0, rjb, "jackknife sub-volumes",
+            OPS(p, subvol, N, jk->M, jk->Rj, 2 * batch, jk->part + ((long)si * 2 + m) * per, st));
+      }
     }
   }
   const sigw::LaunchShape shp = OPS(p, shape, N);
@@ -814,6 +844,110 @@ sigw_status sigw_spectrum_async(sigw_plan p, const int* shells, int n_shells, do
   CKP(p, cudaMemcpyAsync(p->d_Nk, nk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st), "upload Nk");
   p->h2d += sizeof(int) * ns + sizeof(double) * ns;
   return enqueue_spectrum(p, sh, p->d_shells, p->d_Nk, out);
+}
+
+sigw_status sigw_spectrum_jackknife(sigw_plan p, const int* shells, int n_shells, int M, double* omega,
+                                    double* sigma_omega, double* PA, double* sigma_PA, double* PB, double* sigma_PB) {
+  if (!p) return SIGW_EINVAL;
+  if (!p->generated) return fail(p, SIGW_ESTATE, "sigw_spectrum_jackknife before sigw_generate");
+  const int N = p->N, H = N / 2;
+  if (M < 2 || N % M != 0) return fail(p, SIGW_EINVAL, "jackknife: N must be a multiple of M >= 2");
+  std::vector<int> sh;
+  if (shells) {
+    if (n_shells < 1 || n_shells > H) return fail(p, SIGW_EINVAL, "n_shells out of range");
+    sh.assign(shells, shells + n_shells);
+  } else {
+    for (int s = 1; s < H; ++s) sh.push_back(s);
+  }
+  for (int s : sh)
+    if (s < 1 || s >= H) return fail(p, SIGW_EINVAL, "jackknife shells are 1..N/2-1 (no Nyquist shell)");
+  const int ns = (int)sh.size(), batch = p->generated;
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  cudaStream_t st = p->st;
+  const size_t NN = (size_t)N * N, cel = p->celem();
+  const int M3 = M * M * M, sv = N / M;
+  const size_t per = (size_t)2 * batch * M3 * sv;  // partials per (shell, kernel)
+  Jackknife jk;
+  jk.M = M;
+  jk.Xj = p->d_work;
+  jk.Yj = (char*)jk.Xj + (size_t)2 * batch * NN * (H + 1) * cel;
+  jk.Rj = (char*)jk.Yj + (size_t)2 * batch * NN * H * cel;
+  {
+    void* q = nullptr;
+    sigw_status s = dev_alloc(p, &q, sizeof(double) * per * 2 * ns);
+    if (s != SIGW_OK) return s;
+    jk.part = (double*)q;
+  }
+  auto release = [&]() {  // the buffer lives for this call only
+    p->allocs.erase(std::remove(p->allocs.begin(), p->allocs.end(), (void*)jk.part), p->allocs.end());
+    cudaFree(jk.part);
+  };
+  std::vector<double> nk(ns);
+  for (int i = 0; i < ns; ++i) nk[i] = p->Nk[sh[i]];
+  sigw_status s = SIGW_OK;
+  if (cudaMemcpyAsync(p->d_shells, sh.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(p->d_Nk, nk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    s = cuda_fail(p, cudaGetLastError(), "upload shells");
+  p->h2d += sizeof(int) * ns + sizeof(double) * ns;
+  if (s == SIGW_OK) s = enqueue_spectrum(p, sh, p->d_shells, p->d_Nk, p->d_out, &jk);
+  std::vector<double> part(per * 2 * ns), res((size_t)batch * ns * 4);
+  if (s == SIGW_OK &&
+      (cudaMemcpyAsync(part.data(), jk.part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaMemcpyAsync(res.data(), p->d_out, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    s = cuda_fail(p, cudaGetLastError(), "jackknife download");
+  p->d2h += sizeof(double) * (part.size() + res.size());
+  release();
+  if (s != SIGW_OK) return s;
+  if ((s = check_err_flag(p)) != SIGW_OK) return s;
+  // host: E[m][sub] per (realisation, shell), leave-one-out replicas, jackknife variance (FP64, fixed order)
+  const double L = p->L, V = L * L * L, dx = L / N;
+  for (int b = 0; b < batch; ++b)
+    for (int si = 0; si < ns; ++si) {
+      const int n_c = sh[si];
+      const double C = 4.0 * dx * dx * dx / ((double)n_c * n_c * V * V);
+      const double norm = C * C / ((double)NN * N * V * p->Nk[n_c]);
+      const double kc = n_c * 2.0 * kPi / L;
+      std::vector<double> rep[3];
+      double Etot[2] = {0.0, 0.0};
+      std::vector<double> E[2] = {std::vector<double>(M3, 0.0), std::vector<double>(M3, 0.0)};
+      for (int m = 0; m < 2; ++m)
+        for (int f = 0; f < 2; ++f)
+          for (int u = 0; u < M3; ++u) {
+            const double* q = part.data() + ((size_t)(si * 2 + m) * 2 * batch + (size_t)(b * 2 + f)) * M3 * sv +
+                              (size_t)u * sv;
+            double t = 0.0;
+            for (int x = 0; x < sv; ++x) t += q[x];
+            E[m][u] += t;
+          }
+      for (int m = 0; m < 2; ++m)
+        for (int u = 0; u < M3; ++u) Etot[m] += E[m][u];
+      for (int u = 0; u < M3; ++u) {
+        const double pa = norm * (Etot[0] - E[0][u]) / (1.0 - 1.0 / M3);
+        const double pb = norm * (Etot[1] - E[1][u]) / (1.0 - 1.0 / M3);
+        rep[0].push_back(pa);
+        rep[1].push_back(pb);
+        rep[2].push_back(kc * kc * kc / (48.0 * kPi * kPi) * (pa + pb));
+      }
+      double mean[3], sig[3];
+      for (int q = 0; q < 3; ++q) {
+        double mu = 0.0;
+        for (double v : rep[q]) mu += v;
+        mu /= M3;
+        double ss = 0.0;
+        for (double v : rep[q]) ss += (v - mu) * (v - mu);
+        mean[q] = mu;
+        sig[q] = std::sqrt((double)(M3 - 1) / M3 * ss);
+      }
+      const size_t o = (size_t)b * ns + si;
+      if (PA) PA[o] = mean[0];
+      if (PB) PB[o] = mean[1];
+      if (omega) omega[o] = mean[2];
+      if (sigma_PA) sigma_PA[o] = sig[0];
+      if (sigma_PB) sigma_PB[o] = sig[1];
+      if (sigma_omega) sigma_omega[o] = sig[2];
+    }
+  return SIGW_OK;
 }
 
 sigw_status sigw_spectrum(sigw_plan p, const int* shells, int n_shells, double* omega, double* PA, double* PB,

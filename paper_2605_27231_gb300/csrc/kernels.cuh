@@ -739,9 +739,10 @@ __global__ void __launch_bounds__(256) k_f2(const cx<T>* __restrict__ F, cx<T>* 
   }
 }
 
-// sum over the two polarisations of |e^l_ij(k_hat) S_ij|^2 (Sec. sec_sigw basis: u = k x e0 / |k x e0|,
-// e1 in place of e0 when k is parallel to e0, v = k x u).  S = (00, 11, 22, 01, 02, 12).
-__device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2* S) {
+// The two TT amplitudes e^+_ij(k_hat) S_ij and e^x_ij(k_hat) S_ij (Sec. sec_sigw basis: u = k x e0 / |k x e0|,
+// e1 in place of e0 when k is parallel to e0, v = k x u; e^+ = (uu - vv)/sqrt2, e^x = (uv + vu)/sqrt2).
+// S = (00, 11, 22, 01, 02, 12).
+__device__ __forceinline__ void tt_amp(int n0, int n1, int n2, const double2* S, double2& ap, double2& ax) {
   const double nn = sqrt((double)(n0 * n0 + n1 * n1 + n2 * n2));
   const double k0 = n0 / nn, k1 = n1 / nn, k2 = n2 / nn;
   double u0 = 0.0, u1 = k2, u2 = -k1;  // k x e0
@@ -767,19 +768,27 @@ __device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2
     return make_double2(re, im);
   };
   const double2 uu = sdot(u0, u1, u2, u0, u1, u2), vv = sdot(v0, v1, v2, v0, v1, v2), uv = sdot(u0, u1, u2, v0, v1, v2);
-  const double pr = (uu.x - vv.x) * 0.70710678118654752440, pi = (uu.y - vv.y) * 0.70710678118654752440;
-  const double xr = uv.x * 1.41421356237309504880, xi = uv.y * 1.41421356237309504880;
-  return pr * pr + pi * pi + xr * xr + xi * xi;
+  ap = make_double2((uu.x - vv.x) * 0.70710678118654752440, (uu.y - vv.y) * 0.70710678118654752440);
+  ax = make_double2(uv.x * 1.41421356237309504880, uv.y * 1.41421356237309504880);
+}
+// sum over the two polarisations of |e^l_ij(k_hat) S_ij|^2
+__device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2* S) {
+  double2 ap, ax;
+  tt_amp(n0, n1, n2, S, ap, ax);
+  return ap.x * ap.x + ap.y * ap.y + ax.x * ax.x + ax.y * ax.y;
 }
 
 // F3: forward DFT along axis 0 of the six components for a tile of columns (n1 fixed, n2 = k2),
 // TT projection on the modes of shell n_c and the FP64 sum, one partial per CTA.
 // Half-spectrum weight: a stored mode with 0 < k2 < H also stands for its partner wrap(-n), whose
 // direction is -n_hat except on Nyquist indices; the partner is projected with its own direction.
+// With Xj (jackknife), the amplitudes of the stored shell modes are also written to the standard half spectra
+// Xj[b][0] = e^+ : S and Xj[b][1] = -i e^x : S (both Hermitian in this basis away from the Nyquist shell),
+// [b][f][k0][k1][k2], k2 = 0..N/2; every other entry is left as it is (zero).
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_c, int n1lo, int nk1,
                                             double* __restrict__ partial, long pbstride,
-                                            const cx<T>* __restrict__ tw) {
+                                            const cx<T>* __restrict__ tw, cx<T>* __restrict__ Xj) {
   using SH = Shape<T, N>;
   constexpr int E = SH::E3, P = SH::P3, TC = SH::TC3, H = N / 2;
   using Lay = ColLayout<T, N, TC, E>;
@@ -820,7 +829,15 @@ __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_
         double2 S[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) S[q] = make_double2((double)X[q][r].x, (double)X[q][r].y);
-        acc += tt_power(n0, n1, n2, S);
+        double2 ap, ax;
+        tt_amp(n0, n1, n2, S, ap, ax);
+        acc += ap.x * ap.x + ap.y * ap.y + ax.x * ax.x + ax.y * ax.y;
+        if (Xj) {
+          constexpr long NNH = (long)N * N * (H + 1);
+          const long o = ((long)b * 2 * N + (j + r * P)) * N * (H + 1) + (long)((n1 + N) % N) * (H + 1) + n2;
+          Xj[o] = mk<T>((T)ap.x, (T)ap.y);
+          Xj[o + NNH] = mk<T>((T)ax.y, (T)-ax.x);
+        }
         if (n2 > 0 && n2 < H) {
           const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
           acc += tt_power(p0, p1, -n2, S);
@@ -835,6 +852,33 @@ __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
     partial[(long)b * pbstride + blk] = t;
+  }
+}
+
+// Jackknife sub-volume energies: for field f (blockIdx.y) of R[f][x0][x1][x2] and sub-volume `sub` of the M^3
+// blocks of s = N/M cells per side, CTA (sub, t) sums R^2 over the plane x0 = a s + t of that block in FP64:
+// out[(f * M^3 + sub) * s + t].
+template <typename T>
+__global__ void __launch_bounds__(256) k_subvol(const T* __restrict__ R, int N, int M, double* __restrict__ out) {
+  __shared__ double red[8];
+  const int s = N / M;
+  const int t = blockIdx.x % s, sub = blockIdx.x / s;
+  const int a = sub / (M * M), bb = (sub / M) % M, c = sub % M;
+  const long f = blockIdx.y;
+  const T* plane = R + (f * N + (long)a * s + t) * N * N;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int x1 = bb * s + e / s, x2 = c * s + e % s;
+    const double v = (double)plane[(long)x1 * N + x2];
+    acc += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
+    out[(f * M * M * M + sub) * s + t] = tot;
   }
 }
 

@@ -59,9 +59,12 @@ struct OpsRT {
                         const void* tw, int* err, int variant, cudaStream_t st);
   // forward pass along axis 1 keeping |n1| <= n_c
   static cudaError_t f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st);
-  // forward pass along axis 0 + TT projection + shell sum -> per-CTA FP64 partials
+  // forward pass along axis 0 + TT projection + shell sum -> per-CTA FP64 partials; with Xj (nullable) also the
+  // two TT amplitudes of every stored shell mode into the zeroed standard half spectra Xj[batch][2]
   static cudaError_t f3(int N, const void* F2, int n_c, double* partial, long pbstride, int batch, const void* tw,
-                        cudaStream_t st);
+                        cudaStream_t st, void* Xj = nullptr);
+  // jackknife: sum of R^2 over each x0-plane of each of the M^3 sub-volumes, out[field][M^3][N/M]
+  static cudaError_t subvol(int N, int M, const void* R, int nfields, double* out, cudaStream_t st);
 };
 
 extern template struct OpsRT<float>;

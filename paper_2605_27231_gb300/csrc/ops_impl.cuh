@@ -143,7 +143,7 @@ struct OpsT {
   }
   template <int N>
   static cudaError_t f3_n(const void* F2, int n_c, double* partial, long pbs, int batch, const void* tw,
-                          cudaStream_t st) {
+                          cudaStream_t st, void* Xj) {
     using SH = Shape<T, N>;
     const size_t sm = col_bytes<N, SH::TC3, SH::E3>();
     auto k = k_f3<T, N>;
@@ -151,7 +151,7 @@ struct OpsT {
     int lo, nk1;
     n1_range(N, n_c, &lo, &nk1);
     dim3 grid((n_c + 1 + SH::TC3 - 1) / SH::TC3, nk1, batch);
-    k<<<grid, SH::TC3 * SH::P3, sm, st>>>((const C*)F2, n_c, lo, nk1, partial, pbs, (const C*)tw);
+    k<<<grid, SH::TC3 * SH::P3, sm, st>>>((const C*)F2, n_c, lo, nk1, partial, pbs, (const C*)tw, (C*)Xj);
     return cudaGetLastError();
   }
   template <int N>
@@ -299,8 +299,15 @@ cudaError_t OpsRT<T>::f2(int N, const void* F, void* F2, int n_c, int batch, con
 }
 template <typename T>
 cudaError_t OpsRT<T>::f3(int N, const void* F2, int n_c, double* partial, long pbs, int batch, const void* tw,
-                      cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template f3_n<NN>(F2, n_c, partial, pbs, batch, tw, st)));
+                      cudaStream_t st, void* Xj) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template f3_n<NN>(F2, n_c, partial, pbs, batch, tw, st, Xj)));
+}
+template <typename T>
+cudaError_t OpsRT<T>::subvol(int N, int M, const void* R, int nfields, double* out, cudaStream_t st) {
+  if (M < 2 || N % M) return cudaErrorInvalidValue;
+  dim3 grid(M * M * M * (N / M), nfields);
+  k_subvol<T><<<grid, 256, 0, st>>>((const T*)R, N, M, out);
+  return cudaGetLastError();
 }
 
 

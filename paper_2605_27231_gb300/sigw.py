@@ -108,6 +108,8 @@ def lib():
         "sigw_target_box": (C.c_int, [C.c_int, C.c_double, C.POINTER(PZeta), C.c_double, _dbl, C.POINTER(C.c_int)]),
         "sigw_plan_set_box": (C.c_int, [P, C.c_double]),
         "sigw_decomposition_error": (C.c_int, [C.POINTER(Opts), C.c_int, _dbl, _dbl, _dbl]),
+        "sigw_spectrum_jackknife": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, C.c_int, _dbl, _dbl, _dbl, _dbl, _dbl,
+                                              _dbl]),
         "sigw_target_scan": (C.c_int, [P, C.POINTER(PZeta), C.POINTER(NGMap), C.c_uint64, _dbl, C.c_int, C.c_double,
                                        _dbl, _dbl, C.POINTER(C.c_int)]),
     }
@@ -282,6 +284,18 @@ class Plan:
                                    _ptr(out["PA"], C.c_double), _ptr(out["PB"], C.c_double), _ptr(nk, C.c_int64)),
                self._h, "sigw_spectrum")
         out["Nk"] = nk
+        out["n_c"] = sh
+        return out
+
+    def spectrum_jackknife(self, shells=None, M=4):
+        """sigw_spectrum_jackknife; dict of [batch, n_shells] arrays: omega, sigma_omega, PA, sigma_PA, PB,
+        sigma_PB (and n_c).  shells default to 1..N/2-1."""
+        sh = np.arange(1, self.N // 2, dtype=np.int32) if shells is None else np.ascontiguousarray(shells, dtype=np.int32)
+        ns = len(sh)
+        keys = ("omega", "sigma_omega", "PA", "sigma_PA", "PB", "sigma_PB")
+        out = {k: np.zeros((self.batch, ns)) for k in keys}
+        _check(lib().sigw_spectrum_jackknife(self._h, _ptr(sh, C.c_int), ns, M, *[_ptr(out[k], C.c_double) for k in keys]),
+               self._h, "sigw_spectrum_jackknife")
         out["n_c"] = sh
         return out
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 from scipy import integrate
 
-from oracle import brute, decomposition, kernels, philox, semi_analytic, sigw, synth, wick
+from oracle import brute, decomposition, jackknife, kernels, philox, semi_analytic, sigw, synth, wick
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -414,3 +414,40 @@ def test_truncation_error_is_the_eigenvalue_tail():
             assert 0 < mx <= 1 and 0 < gap <= 1
         errs = [decomposition.truncation_error(d, m, k)[0] for k in range(1, 80)]
         assert np.all(np.diff(errs) <= 1e-15)
+
+
+# ---------------------------------------------------------------- jackknife (Sec. sec_envelope_obs)
+def test_jackknife_replica_mean_is_the_shell_estimator(dec):
+    """The mean of the leave-one-out replicas equals the k-space shell average (Parseval links the real-space
+    energies to sum_k |X_k|^2), in every offered shell."""
+    N, L = 16, 1.0
+    Phi, _ = synth.phi_tilde(N, L, 2e-2, 0.5, 4 * 2 * np.pi / L, seed=21, kind="local", F_NL=2.0)
+    j = jackknife.jackknife(Phi, L, dec, shells=[1, 3, 7], M=4)
+    o = sigw.omega(Phi, L, dec, shells=[1, 3, 7])
+    for k in ("PA", "PB", "omega"):
+        np.testing.assert_allclose(j[k], o[k], rtol=1e-12)
+    assert np.all(j["sigma_omega"] > 0) and np.all(j["sigma_omega"] < j["omega"])
+
+
+def test_jackknife_variance_is_the_squared_standard_error():
+    """For replicas of a mean, the jackknife variance equals the squared standard error of the per-sub-volume
+    estimates P_i = M^3 E_i / (V N_k) (a classical identity, independent of the replica formula)."""
+    rng = np.random.default_rng(3)
+    N, M = 16, 4
+    X = rng.standard_normal((N, N, N)) + 1j * rng.standard_normal((N, N, N))
+    E = jackknife.subvolume_energies(X, M)
+    n3 = M ** 3
+    assert abs(E.sum() - np.sum(np.abs(X) ** 2)) < 1e-9 * E.sum()  # Parseval
+    rep = (E.sum() - E) / (1 - 1 / n3)
+    per = n3 * E
+    assert abs(jackknife.jackknife_sigma(rep) - per.std(ddof=1) / np.sqrt(n3)) < 1e-10 * per.mean()
+
+
+def test_jackknife_single_mode_has_no_spread():
+    """One Fourier mode has a uniform real-space energy density: every replica is equal, sigma = 0."""
+    N, M = 16, 4
+    X = np.zeros((N, N, N), dtype=np.complex128)
+    X[3, 5, 2] = 2.0 - 1.0j
+    E = jackknife.subvolume_energies(X, M)
+    np.testing.assert_allclose(E, E.mean(), rtol=1e-12)
+    assert jackknife.jackknife_sigma((E.sum() - E)) < 1e-12 * E.sum()

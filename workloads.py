@@ -35,7 +35,7 @@ class Spec:
     G_NL: float = 0.0
     usr_floor: float = 1e-6
     seed: int = 1
-    alpha_NL: float = 0.0  # non-local map coefficients (Eq. eq_nonlocal), in units of 1 / k*^2
+    alpha_NL: float = 0.0  # non-local map coefficients of Eq. eq_nonlocal (dimensionless; the map divides by k*^2)
     beta_NL: float = 0.0
 
     def as_dict(self):
