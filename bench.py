@@ -126,7 +126,8 @@ def run_ours(args):
     base = list(workloads.USR256_SEEDS) if args.workload == "usr256" else [spec.seed + i for i in range(batch)]
     seeds = shard.seeds_for_rank((base * batch)[:batch], rank, ws)
     stream = torch.cuda.Stream()
-    plan = sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=32, max_batch=batch, n_alpha=args.n_alpha)
+    plan = sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=args.precision, max_batch=batch,
+                     n_alpha=args.n_alpha, alpha_batch=args.alpha_batch)
     n_sh = spec.N // 2
     dev_out = torch.empty(batch * n_sh * 4, dtype=torch.float64, device="cuda")
 
@@ -238,7 +239,8 @@ def run_ours(args):
             "metric": "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path)",
             "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
+            "dtype": "f32" if args.precision == 32 else "f64",
+            "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
             "config": {"workload": args.workload, "N": spec.N, "L": spec.L, "A": spec.A, "sigma": spec.sigma,
                        "kstar_over_kf": round(spec.kstar * spec.L / (2 * 3.141592653589793), 6), "map": spec.kind,
                        "seeds_per_step": batch, "shells": n_sh, "n_alpha": args.n_alpha, "n_modes": 200,
@@ -433,6 +435,10 @@ def main():
     ap.add_argument("--cpu-terms", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paper-scan", action="store_true")
+    ap.add_argument("--alpha-batch", type=int, default=0,
+                    help="separable terms per strided-pass launch (0: chosen by the autotuner)")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64],
+                    help="working precision of the main leg (64 only for profiling the FP64 path)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-slots", type=int, default=3)

@@ -228,7 +228,7 @@ sigw_status sigw_server_destroy(sigw_server srv);
 
 /* Autotuner (no counterpart in the paper).  On the plan's current field, times the two strided inverse passes of
  * one target shell (n_c; 0 picks N/4) for every candidate choice: terms per launch in {4, 5, 8, 10, 16} (at most
- * n_alpha, and at most opts->alpha_batch when that is set) and, where two exist (FP32, N >= 128), both radix
+ * n_alpha; exactly opts->alpha_batch when that is set) and, where two exist (FP32, N >= 128), both radix
  * variants of the strided passes.  Keeps the fastest in the plan and in a process-wide table keyed by
  * (N, precision, max_batch, n_alpha) from which later plans with alpha_batch = 0 start; then times both radix
  * forms of the last inverse pass (FP32, N = 128 and 256) on the terms just produced.  Outputs nullable: chosen

@@ -1048,6 +1048,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
     return SIGW_OK;
   };
   for (int B : cands) {
+    if (p->opts.alpha_batch > 0) B = bmax;  // terms per launch fixed by the options: tune the radices only
     if (B > bmax || status != SIGW_OK) continue;
     float t1[2] = {1e30f, 1e30f}, t2[2] = {1e30f, 1e30f};
     for (int v = 0; v < nvar && status == SIGW_OK; ++v) {
@@ -1062,6 +1063,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
       bestB = B;
       bestV = v1 | (v2 << 2);
     }
+    if (p->opts.alpha_batch > 0) break;
   }
   // last inverse pass: radix variants on the W just produced by the best strided choice
   int bestP3 = 0;

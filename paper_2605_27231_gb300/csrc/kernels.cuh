@@ -533,10 +533,11 @@ template <typename T, int N, int E_ = ((N >= 16) ? 8 : 4)> struct P3Cfg {
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-// Radix-16 alternative of the last inverse pass (autotuner variant bit 2): FP32, N = 128 and 256, where it needs
-// one shared-memory exchange per transform instead of two.
+// Radix-16 alternative of the last inverse pass (autotuner variant bit 2), FP32.  N = 128, 256: one
+// shared-memory exchange per transform instead of two.  N = 512: two exchanges either way, but a row is one
+// warp (P = 32), so the exchanges need warp barriers only (the radix-8 form uses 64 threads and block barriers).
 template <typename T, int N> struct AltP3 {
-  static constexpr bool exists = sizeof(T) == 4 && (N == 128 || N == 256);
+  static constexpr bool exists = sizeof(T) == 4 && (N == 128 || N == 256 || N == 512);
   static constexpr int E = 16;
 };
 

@@ -255,6 +255,7 @@ template <typename T>
 int OpsRT<T>::p3_variants(int N) {
   if (N == 128) return AltP3<T, 128>::exists ? 2 : 1;
   if (N == 256) return AltP3<T, 256>::exists ? 2 : 1;
+  if (N == 512) return AltP3<T, 512>::exists ? 2 : 1;
   return 1;
 }
 template <typename T>

@@ -171,6 +171,25 @@ def test_batch_equals_single_bitwise(lib):
         assert np.array_equal(batched[i], single)
 
 
+def test_degenerate_inputs(lib, dec):
+    """A = 0 gives an exactly zero field and spectrum; one separable term; shells in any order with repeats give
+    the values of the sorted call; an empty shell list is rejected."""
+    with lib.Plan(16, 1.0, n_alpha=2, precision=32) as p:
+        p.generate(0.0, 0.5, 4 * 2 * np.pi, kind="local", F_NL=3.0)
+        r = p.spectrum()
+        assert np.all(r["omega"] == 0.0) and np.all(r["PA"] == 0.0)
+        import ctypes
+        one = (ctypes.c_int * 1)(1)
+        assert lib.lib().sigw_spectrum(p._h, one, 0, None, None, None, None) == lib.EINVAL
+    spec = workloads.Spec(N=16, L=1.0, A=2e-2, sigma=0.5, kstar=4 * 2 * np.pi, kind="usr", seed=17)
+    d1 = odec.build(n_alpha=1)
+    ref, _, _ = _oracle(spec, d1, [2, 5, 8])
+    with lib.Plan(16, 1.0, precision=64, n_alpha=1) as p:
+        p.generate_spec(spec)
+        got = p.spectrum([8, 2, 5, 2])["omega"][0]
+    np.testing.assert_allclose(got, ref["omega"][[2, 0, 1, 0]], rtol=1e-9)
+
+
 def test_state_errors(lib):
     with lib.Plan(16, 1.0, n_alpha=2) as p:
         with pytest.raises(lib.SigwError) as e:
