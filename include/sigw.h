@@ -238,6 +238,11 @@ sigw_status sigw_server_destroy(sigw_server srv);
  * Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */
 sigw_status sigw_plan_autotune(sigw_plan plan, int n_c, int* out_alpha_batch, int* out_variant, double* out_ms);
 
+/* Sets the tuned choices directly (for example to replay a choice sigw_plan_autotune made in another process):
+ * terms per launch in [1, the plan's maximum] and the variant bits of sigw_plan_autotune (bits for variants the
+ * plan's N and precision lack are ignored).  Errors: SIGW_EINVAL. */
+sigw_status sigw_plan_set_tuning(sigw_plan plan, int alpha_batch, int variant);
+
 /* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter,
  * gradient), 2 second inverse pass, 3 last inverse pass + product + first forward pass, 4 second forward
  * pass, 5 last forward pass + TT projection + shell sum, 6 bin finalisation. */

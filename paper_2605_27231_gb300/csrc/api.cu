@@ -1173,6 +1173,21 @@ sigw_status sigw_target_scan(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap
   return SIGW_OK;
 }
 
+sigw_status sigw_plan_set_tuning(sigw_plan p, int alpha_batch, int variant) {
+  if (!p) return SIGW_EINVAL;
+  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 7)
+    return fail(p, SIGW_EINVAL, "sigw_plan_set_tuning: alpha_batch or variant out of range");
+  CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
+  CKP(p, cudaStreamSynchronize(p->st), "set_tuning");
+  p->B = alpha_batch;
+  p->variant = variant;
+  if (p->graph) {  // the captured loop used the old choice
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  return SIGW_OK;
+}
+
 sigw_status sigw_plan_profile(sigw_plan p, int enable) {
   if (!p) return SIGW_EINVAL;
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");

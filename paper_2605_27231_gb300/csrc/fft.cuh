@@ -101,6 +101,41 @@ template <typename T, int DIR> __device__ __forceinline__ void dft16(cx<T>* v) {
   }
 }
 
+// radix-2 split of a 32-point DFT into two 16-point DFTs; the odd half is rotated by W_32^k (k = 1..15),
+// written with the cos/sin of k pi / 16 and the symmetries of the first octant.
+template <typename T, int DIR> __device__ __forceinline__ void dft32(cx<T>* v) {
+  const T c1 = (T)0.98078528040323044913, s1 = (T)0.19509032201612826785;  // pi/16
+  const T c2 = (T)0.92387953251128675613, s2 = (T)0.38268343236508977173;  // pi/8
+  const T c3 = (T)0.83146961230254523708, s3 = (T)0.55557023301960222474;  // 3 pi/16
+  const T h = (T)0.70710678118654752440;                                    // pi/4
+  cx<T> e[16], o[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+  dft16<T, DIR>(e);
+  dft16<T, DIR>(o);
+  // o[k] times W_32^k = e^{i DIR k pi / 16}: rot<T, DIR>(a, c, s) multiplies by c + i DIR s
+  o[1] = rot<T, DIR>(o[1], c1, s1);
+  o[2] = rot<T, DIR>(o[2], c2, s2);
+  o[3] = rot<T, DIR>(o[3], c3, s3);
+  o[4] = rot<T, DIR>(o[4], h, h);
+  o[5] = rot<T, DIR>(o[5], s3, c3);
+  o[6] = rot<T, DIR>(o[6], s2, c2);
+  o[7] = rot<T, DIR>(o[7], s1, c1);
+  o[8] = mul_i<T, DIR>(o[8]);
+  o[9] = rot<T, DIR>(o[9], -s1, c1);
+  o[10] = rot<T, DIR>(o[10], -s2, c2);
+  o[11] = rot<T, DIR>(o[11], -s3, c3);
+  o[12] = rot<T, DIR>(o[12], -h, h);
+  o[13] = rot<T, DIR>(o[13], -c3, s3);
+  o[14] = rot<T, DIR>(o[14], -c2, s2);
+  o[15] = rot<T, DIR>(o[15], -c1, s1);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    v[k] = add<T>(e[k], o[k]);
+    v[k + 16] = sub<T>(e[k], o[k]);
+  }
+}
+
 template <typename T, int DIR, int R> __device__ __forceinline__ void dftR(cx<T>* v) {
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
@@ -111,6 +146,8 @@ template <typename T, int DIR, int R> __device__ __forceinline__ void dftR(cx<T>
     dft8<T, DIR>(v);
   } else if constexpr (R == 16) {
     dft16<T, DIR>(v);
+  } else if constexpr (R == 32) {
+    dft32<T, DIR>(v);
   } else {
     static_assert(R == 16, "unsupported radix");
   }
@@ -150,16 +187,18 @@ template <typename T, int N, bool ONE = false, int PADSH = 3> struct RowLayout {
   __device__ __forceinline__ int idx(int p) const { return p + (p >> PADSH); }
 };
 
-template <typename T, int N, int TC, int E> struct ColLayout {
-  static constexpr bool SINGLE = false;
+// ONE: a single buffer (a stage syncs between its reads and writes), for tiles whose two buffers would not
+// leave room for a second CTA per SM.
+template <typename T, int N, int TC, int E, bool ONE = false> struct ColLayout {
+  static constexpr bool SINGLE = ONE;
   static constexpr int PER_PHASE = 128 / (int)sizeof(cx<T>);
   static constexpr int G0 = PER_PHASE / TC;
   static constexpr int G = G0 < 1 ? 1 : G0;
   static constexpr int BUF = N * TC;
-  static constexpr int SIZE = 2 * BUF;  // elements for all TC pencils (both buffers)
+  static constexpr int SIZE = ONE ? BUF : 2 * BUF;  // elements for all TC pencils
   cx<T>* base;  // shared by the TC pencils of the CTA
   int c;
-  __device__ __forceinline__ cx<T>* buf(int which) const { return base + which * BUF; }
+  __device__ __forceinline__ cx<T>* buf(int which) const { return ONE ? base : base + which * BUF; }
   __device__ __forceinline__ int idx(int p) const {
     if constexpr (G == 1) {
       return p * TC + c;

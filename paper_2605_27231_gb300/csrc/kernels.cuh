@@ -75,14 +75,19 @@ template <typename T, int N> struct Shape {
   static constexpr int TC3 = TC3_1 * P3 < 32 ? 32 / P3 : TC3_1;  // whole warps (the partial sum uses shuffles)
 };
 
-// Alternative radix of the strided inverse passes (autotuner variant 1): FP32, N >= 128 only.
+// Alternative radix of the strided inverse passes (autotuner variant 1): FP32, N >= 128 only.  At N = 512 the
+// alternative is radix 32 (two stages, one exchange, 16-column tiles) instead of radix 16 (three stages).
 template <typename T, int N> struct AltStrided {
   static constexpr bool exists = sizeof(T) == 4 && N >= 128;
-  static constexpr int E = Shape<T, N>::ES == 16 ? 8 : 16;
+  static constexpr int E = N == 512 ? 32 : (Shape<T, N>::ES == 16 ? 8 : 16);
   static constexpr int P = N / E;
   static constexpr int TC0 = 256 / P;
   static constexpr int TC = TC0 > N / 2 ? N / 2 : TC0;
 };
+
+// Column-tile exchange layout of the strided passes: one buffer when E >= 32 (a radix-32 pencil of 512
+// points would otherwise need 128 KB for a 16-column tile).
+template <typename T, int N, int TC, int E> using StridedLay = ColLayout<T, N, TC, E, (E >= 32)>;
 
 template <int P> struct RowSync { using type = SyncWarp; };
 template <> struct RowSync<64> { using type = SyncBlock; };
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
                                             const T* __restrict__ phitab, int nm1, int alpha0, int nb,
                                             const cx<T>* __restrict__ tw) {
   constexpr int E = E_, P = N / E_, TC = TC_, H = N / 2, NH = H + 1;
-  using Lay = ColLayout<T, N, TC, E>;
+  using Lay = StridedLay<T, N, TC, E>;
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(smraw) + Lay::SIZE;  // N values (column 0 only)
   int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);              // N cells
@@ -437,11 +442,11 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
 //   W[2] = IDFT_1[Tb]            (G_0)
 // One value array is live at a time (the Ta tile is reloaded through L1 for the second transform).
 template <typename T, int N, int E_ = Shape<T, N>::ES, int TC_ = Shape<T, N>::TC>
-__global__ void __launch_bounds__(256, 2) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
+__global__ void __launch_bounds__(256, (E_ >= 32 ? 1 : 2)) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
                                                cx<T>* __restrict__ W, int n_alpha, int alpha0, int nb,
                                                const cx<T>* __restrict__ tw) {
   constexpr int E = E_, P = N / E_, TC = TC_, H = N / 2;
-  using Lay = ColLayout<T, N, TC, E>;
+  using Lay = StridedLay<T, N, TC, E>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
   const Lay L{reinterpret_cast<cx<T>*>(smraw), c};

@@ -25,6 +25,8 @@ struct OpsT {
   static size_t row_bytes(int count) { return (size_t)count * RowLayout<T, N>::SIZE * sizeof(C); }
   template <int N, int TC, int E>
   static size_t col_bytes() { return (size_t)ColLayout<T, N, TC, E>::SIZE * sizeof(C); }
+  template <int N, int TC, int E>
+  static size_t strided_bytes() { return (size_t)StridedLay<T, N, TC, E>::SIZE * sizeof(C); }
 
   // ------------------------------------------------------------ synthesis
   template <int N, int MODE>
@@ -65,7 +67,7 @@ struct OpsT {
   template <int N, int E, int TC>
   static cudaError_t p1_v(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
                           int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
-    const size_t sm = col_bytes<N, TC, E>() + N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
+    const size_t sm = strided_bytes<N, TC, E>() + N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
     auto k = k_p1<T, N, E, TC>;
     SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
     dim3 grid((N / 2) / TC, N, batch);
@@ -87,7 +89,7 @@ struct OpsT {
   template <int N, int E, int TC>
   static cudaError_t p2_v(const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
                           const void* tw, cudaStream_t st) {
-    const size_t sm = col_bytes<N, TC, E>();
+    const size_t sm = strided_bytes<N, TC, E>();
     auto k = k_p2<T, N, E, TC>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     dim3 grid((N / 2) / TC, N, batch * nb);

@@ -107,6 +107,7 @@ def lib():
         "sigw_plan_profile_read": (C.c_int, [P, C.POINTER(Profile)]),
         "sigw_target_box": (C.c_int, [C.c_int, C.c_double, C.POINTER(PZeta), C.c_double, _dbl, C.POINTER(C.c_int)]),
         "sigw_plan_set_box": (C.c_int, [P, C.c_double]),
+        "sigw_plan_set_tuning": (C.c_int, [P, C.c_int, C.c_int]),
         "sigw_decomposition_error": (C.c_int, [C.POINTER(Opts), C.c_int, _dbl, _dbl, _dbl]),
         "sigw_spectrum_jackknife": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, C.c_int, _dbl, _dbl, _dbl, _dbl, _dbl,
                                               _dbl]),
@@ -336,6 +337,9 @@ class Plan:
         _check(lib().sigw_plan_autotune(self._h, n_c, C.byref(b), C.byref(v), C.byref(ms)), self._h,
                "sigw_plan_autotune")
         return b.value, v.value, ms.value
+
+    def set_tuning(self, alpha_batch, variant):
+        _check(lib().sigw_plan_set_tuning(self._h, alpha_batch, variant), self._h, "sigw_plan_set_tuning")
 
     def profile(self, enable=True):
         _check(lib().sigw_plan_profile(self._h, 1 if enable else 0), self._h, "sigw_plan_profile")

@@ -268,6 +268,12 @@ def test_broad512_small_shells_fp32_fp64(lib, dec):
         np.testing.assert_array_equal(got["Nk"][0], ref["Nk"])
         np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=rtol)
         np.testing.assert_allclose(got["PA"][0], ref["PA"], rtol=rtol)
+    # every radix variant of the FP32 passes at this size (radix 32 strided passes, radix 16 last pass)
+    with lib.Plan(spec.N, spec.L, precision=32) as p:
+        p.generate_spec(spec)
+        for v in (1, 2, 4, 7):
+            p.set_tuning(10, v)
+            np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
 
 
 def test_graph_replay_equals_direct_launches(lib):
@@ -284,6 +290,22 @@ def test_graph_replay_equals_direct_launches(lib):
         g3 = p.spectrum()["omega"]
     assert np.array_equal(direct, g1) and np.array_equal(g1, g2)
     assert np.array_equal(g3[0], direct[0])
+
+
+@pytest.mark.parametrize("N", [128, 256])
+def test_every_variant_matches_oracle(lib, dec, N):
+    """Each radix variant (bits 1, 2, 4 and all together) on sampled shells of a local-map field, vs the oracle."""
+    spec = workloads.scaled(workloads.workload("local128"), N)
+    shells = [3, N // 4]
+    d10 = odec.build(n_alpha=10)
+    ref, _, _ = _oracle(spec, d10, shells)
+    with lib.Plan(N, spec.L, precision=32, n_alpha=10) as p:
+        p.generate_spec(spec)
+        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)):
+            p.set_tuning(B, v)
+            np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
+        with pytest.raises(lib.SigwError):
+            p.set_tuning(0, 0)
 
 
 def test_autotune_keeps_results_and_seeds_later_plans(lib, dec):
