@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
   }
   __syncthreads();
   const long fstride = (long)N * N * H;  // one field
+  const T fj = (T)j;
   for (int a = 0; a < nb; ++a) {
     const T* tab = sm_tab + a * nm1;
     // D = 0: V_a; D = 1: i n0 V_a.  V_a is formed again for the second transform instead of being kept,
@@ -422,8 +423,8 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
           const cx<T> yn = sm_nyq[k0];
           x = mk<T>(x.x - fn * yn.y, x.y + fn * yn.x);
         }
-        if (D) {
-          const T nd = (T)derivn(j + r * P, N);
+        if (D) {  // n^D(k0) for k0 = j + r P: j < P, so k0 < N/2 exactly when r < E/2 (Nyquist: r = E/2, j = 0)
+          const T nd = r < E / 2 ? fj + (T)(r * P) : ((r == E / 2 && j == 0) ? (T)0 : fj + (T)(r * P - N));
           x = mk<T>(-nd * x.y, nd * x.x);
         }
         v[r] = x;
@@ -546,31 +547,56 @@ template <typename T, int N> struct AltP3 {
   static constexpr int E = 16;
 };
 
-// 1-D Hermitian spectrum value at index k (0..N-1) of a packed row held in shared memory:
-//   plain: k = 0 -> Re row[0], k = H -> Im row[0], else row[k] or conj(row[N-k]);
-//   grad : i n^D(k) times the plain value, zero at k = 0 and k = H (the packed column is not read).
-template <typename T, int N>
-__device__ __forceinline__ cx<T> herm_plain(const cx<T>* row, int k) {
-  constexpr int H = N / 2;
-  if (k == 0) return mk<T>(row[0].x, (T)0);
-  if (k == H) return mk<T>(row[0].y, (T)0);
-  if (k < H) return row[k];
-  return conjg<T>(row[N - k]);
-}
-template <typename T, int N>
-__device__ __forceinline__ cx<T> herm_grad(const cx<T>* row, int k) {
-  constexpr int H = N / 2;
-  if (k == 0 || k == H) return mk<T>((T)0, (T)0);
-  cx<T> x;
-  T n;
-  if (k < H) {
-    x = row[k];
-    n = (T)k;
-  } else {
-    x = conjg<T>(row[N - k]);
-    n = (T)(k - N);
+// 1-D Hermitian spectrum value of a packed row held in shared memory, at the element k = j + r P that thread j
+// (0 <= j < P) holds in its r-th register (r unrolled).  plain: k = 0 -> Re row[0], k = N/2 -> Im row[0], else
+// row[k] or conj(row[N-k]); grad: i n^D(k) times the plain value, zero at k = 0 and k = N/2.
+// With P E = N, k < N/2 exactly when r < E/2, so only j = 0 needs a run-time test (k = 0 and k = N/2 come from
+// the packed column 0), and the wave number of the gradient is (T) j plus a compile-time offset.
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_plain_r(const cx<T>* row, int j, int r) {
+  constexpr int P = N / E;
+  if (r < E / 2) {
+    const cx<T> v = row[j + r * P];
+    return (r == 0 && j == 0) ? mk<T>(v.x, (T)0) : v;
   }
+  const bool hz = (r == E / 2) && (j == 0);
+  const cx<T> v = row[hz ? 0 : (E - r) * P - j];
+  return hz ? mk<T>(v.y, (T)0) : conjg<T>(v);
+}
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_grad_r(const cx<T>* row, int j, int r, T fj) {
+  constexpr int P = N / E;
+  if (r < E / 2) {
+    const cx<T> x = row[j + r * P];
+    const T n = fj + (T)(r * P);
+    return mk<T>(-n * x.y, n * x.x);
+  }
+  const bool hz = (r == E / 2) && (j == 0);
+  const cx<T> x = conjg<T>(row[hz ? 0 : (E - r) * P - j]);
+  const T n = hz ? (T)0 : fj + (T)(r * P - N);
   return mk<T>(-n * x.y, n * x.x);
+}
+
+// One term's contribution sigma g_i g_j to the six product components at one point, with zz = (g2, g1):
+// a0 = s_00, a21 = (s_22, s_11), a43 = (s_02, s_01), a5 = s_12.  FP32 uses paired (FP32x2) multiply-adds.
+template <typename T>
+__device__ __forceinline__ void accum6(T sa, T g0, cx<T> zz, T& a0, cx<T>& a21, cx<T>& a43, T& a5) {
+  const T s0 = sa * g0;
+  const cx<T> t = mk<T>(sa * zz.x, sa * zz.y);
+  a21 = mk<T>(fma(t.x, zz.x, a21.x), fma(t.y, zz.y, a21.y));
+  a43 = mk<T>(fma(s0, zz.x, a43.x), fma(s0, zz.y, a43.y));
+  a0 = fma(s0, g0, a0);
+  a5 = fma(t.y, zz.x, a5);
+}
+template <>
+__device__ __forceinline__ void accum6<float>(float sa, float g0, float2 zz, float& a0, float2& a21, float2& a43,
+                                              float& a5) {
+  const float s0 = sa * g0;
+  const float2 t = __fmul2_rn(zz, make_float2(sa, sa));
+  a21 = __ffma2_rn(t, zz, a21);
+  a43 = __ffma2_rn(make_float2(s0, s0), zz, a43);
+  a0 = __fmaf_rn(s0, g0, a0);
+  a5 = __fmaf_rn(t.y, zz.x, a5);
 }
 
 // P3: last inverse pass (axis 2, C2R) of all terms for RPC consecutive rows, the product
@@ -620,11 +646,14 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
   };
   if (threadIdx.x == 0)
     for (int pr = 0; pr < STAGES - 1 && pr < npairs; ++pr) issue(pr);
-  T acc[6][E];
+  T a0[E], a5[E];
+  cx<T> a21[E], a43[E];
 #pragma unroll
-  for (int q = 0; q < 6; ++q)
-#pragma unroll
-    for (int r = 0; r < E; ++r) acc[q][r] = (T)0;
+  for (int r = 0; r < E; ++r) {
+    a0[r] = a5[r] = (T)0;
+    a21[r] = a43[r] = mk<T>((T)0, (T)0);
+  }
+  const T fj = (T)j;
   bool ok = true;
   for (int pr = 0; pr < npairs; ++pr) {
     const int s = pr % STAGES;
@@ -643,61 +672,41 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
     cx<T> zB[E], z[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      const int k = j + r * P;
-      const cx<T> g0 = herm_plain<T, N>(w20, k);
-      const cx<T> g0b = two ? herm_plain<T, N>(w21, k) : mk<T>((T)0, (T)0);
+      const cx<T> g0 = herm_plain_r<T, N, E>(w20, j, r);
+      const cx<T> g0b = two ? herm_plain_r<T, N, E>(w21, j, r) : mk<T>((T)0, (T)0);
       zB[r] = mk<T>(g0.x - g0b.y, g0.y + g0b.x);
     }
     fft_pencil<T, N, E, +1, Lay, Sync>(zB, j, L, tw, Sync());
     const T sa = sigma[a];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      const int k = j + r * P;
-      const cx<T> g2 = herm_grad<T, N>(wb0, k), g1 = herm_plain<T, N>(w10, k);
+      const cx<T> g2 = herm_grad_r<T, N, E>(wb0, j, r, fj), g1 = herm_plain_r<T, N, E>(w10, j, r);
       z[r] = mk<T>(g2.x - g1.y, g2.y + g1.x);
     }
     fft_pencil<T, N, E, +1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const T g0 = zB[r].x, g1 = z[r].y, g2 = z[r].x;
-      const T s0 = sa * g0, s1 = sa * g1;
-      acc[0][r] += s0 * g0;
-      acc[1][r] += s1 * g1;
-      acc[2][r] += sa * g2 * g2;
-      acc[3][r] += s0 * g1;
-      acc[4][r] += s0 * g2;
-      acc[5][r] += s1 * g2;
-    }
+    for (int r = 0; r < E; ++r) accum6<T>(sa, zB[r].x, z[r], a0[r], a21[r], a43[r], a5[r]);
     if (two) {  // uniform across the CTA
       const T sb = sigma[a + 1];
 #pragma unroll
       for (int r = 0; r < E; ++r) {
-        const int k = j + r * P;
-        const cx<T> h2 = herm_grad<T, N>(wb1, k), h1 = herm_plain<T, N>(w11, k);
+        const cx<T> h2 = herm_grad_r<T, N, E>(wb1, j, r, fj), h1 = herm_plain_r<T, N, E>(w11, j, r);
         z[r] = mk<T>(h2.x - h1.y, h2.y + h1.x);
       }
       fft_pencil<T, N, E, +1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
-      for (int r = 0; r < E; ++r) {
-        const T g0 = zB[r].y, g1 = z[r].y, g2 = z[r].x;
-        const T s0 = sb * g0, s1 = sb * g1;
-        acc[0][r] += s0 * g0;
-        acc[1][r] += s1 * g1;
-        acc[2][r] += sb * g2 * g2;
-        acc[3][r] += s0 * g1;
-        acc[4][r] += s0 * g2;
-        acc[5][r] += s1 * g2;
-      }
+      for (int r = 0; r < E; ++r) accum6<T>(sb, zB[r].y, z[r], a0[r], a21[r], a43[r], a5[r]);
     }
     __syncthreads();  // stage s fully read before it is refilled
   }
-  // forward R2C of the six real rows, two per complex transform
+  // forward R2C of the six real rows (00, 11 | 22, 01 | 02, 12), two per complex transform
   cx<T>* zb = L.buf(0);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     cx<T> z[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) z[r] = mk<T>(acc[2 * q][r], acc[2 * q + 1][r]);
+    for (int r = 0; r < E; ++r)
+      z[r] = q == 0 ? mk<T>(a0[r], a21[r].y) : (q == 1 ? mk<T>(a21[r].x, a43[r].y) : mk<T>(a43[r].x, a5[r]));
     fft_pencil<T, N, E, -1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
     for (int r = 0; r < E; ++r) zb[L.idx(j + r * P)] = z[r];
