@@ -39,6 +39,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 NCU_TRAFFIC_256 = {
     "p1_inv_axis0_filter": (0.068532e9 + 1.281052e9, 0.0676e9 + 20 * 67.108864e6),
     "p2_inv_axis1": (1.073817e9 + 1.553402e9, 40 * 67.108864e6),
+    "p3_inv_axis2_product_fwd_axis2": (2.013373e9 + 0.026424e9, 30 * 67.108864e6 + 6 * 65536 * 2 * 8),
 }
 
 
