@@ -75,7 +75,8 @@ template <typename T, int N> struct Shape {
   static constexpr int TC3 = TC3_1 * P3 < 32 ? 32 / P3 : TC3_1;  // whole warps (the partial sum uses shuffles)
 };
 
-// Alternative radix of the strided inverse passes (autotuner variant 1): FP32, N >= 128 only.  At N = 512 the
+// Alternative radix of the strided inverse passes (variant bit 1 for the first pass; the second pass uses
+// AltStrided2 with bit 4): FP32, N >= 128 only.  At N = 512 the
 // alternative is radix 32 (two stages, one exchange, 16-column tiles) instead of radix 16 (three stages).
 template <typename T, int N> struct AltStrided {
   static constexpr bool exists = sizeof(T) == 4 && N >= 128;
@@ -88,6 +89,14 @@ template <typename T, int N> struct AltStrided {
 // Column-tile exchange layout of the strided passes: one buffer when E >= 32 (a radix-32 pencil of 512
 // points would otherwise need 128 KB for a 16-column tile).
 template <typename T, int N, int TC, int E> using StridedLay = ColLayout<T, N, TC, E, (E >= 32)>;
+
+// Alternative of the second strided pass (variant bit 4): as AltStrided, except at N = 512, where a 512-thread
+// CTA runs 16 columns of radix 16 (full 128-byte row segments, 16 warps per SM, no spills).
+template <typename T, int N> struct AltStrided2 {
+  static constexpr bool exists = sizeof(T) == 4 && N >= 128;
+  static constexpr int E = N == 512 ? 16 : AltStrided<T, N>::E;
+  static constexpr int TC = N == 512 ? 16 : AltStrided<T, N>::TC;
+};
 
 template <int P> struct RowSync { using type = SyncWarp; };
 template <> struct RowSync<64> { using type = SyncBlock; };
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>
 //   W[2] = IDFT_1[Tb]            (G_0)
 // One value array is live at a time (the Ta tile is reloaded through L1 for the second transform).
 template <typename T, int N, int E_ = Shape<T, N>::ES, int TC_ = Shape<T, N>::TC>
-__global__ void __launch_bounds__(256, (E_ >= 32 ? 1 : 2)) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
+__global__ void __launch_bounds__(TC_ * (N / E_), ((E_ >= 32 || TC_ * (N / E_) > 256) ? 1 : 2)) k_p2(const cx<T>* __restrict__ Ta, const cx<T>* __restrict__ Tb,
                                                cx<T>* __restrict__ W, int n_alpha, int alpha0, int nb,
                                                const cx<T>* __restrict__ tw) {
   constexpr int E = E_, P = N / E_, TC = TC_, H = N / 2;
@@ -578,8 +587,9 @@ __device__ __forceinline__ cx<T> herm_grad_r(const cx<T>* row, int j, int r, T f
 }
 
 // One term's contribution sigma g_i g_j to the six product components at one point, with zz = (g2, g1):
-// a0 = s_00, a21 = (s_22, s_11), a43 = (s_02, s_01), a5 = s_12.  FP32 uses paired (FP32x2) multiply-adds.
-template <typename T>
+// a0 = s_00, a21 = (s_22, s_11), a43 = (s_02, s_01), a5 = s_12.  PAIRED (FP32, N <= 256) uses paired (FP32x2)
+// multiply-adds; at N = 512 their aligned register pairs made the radix-16 last pass spill, so it stays scalar.
+template <typename T, bool PAIRED>
 __device__ __forceinline__ void accum6(T sa, T g0, cx<T> zz, T& a0, cx<T>& a21, cx<T>& a43, T& a5) {
   const T s0 = sa * g0;
   const cx<T> t = mk<T>(sa * zz.x, sa * zz.y);
@@ -589,8 +599,8 @@ __device__ __forceinline__ void accum6(T sa, T g0, cx<T> zz, T& a0, cx<T>& a21, 
   a5 = fma(t.y, zz.x, a5);
 }
 template <>
-__device__ __forceinline__ void accum6<float>(float sa, float g0, float2 zz, float& a0, float2& a21, float2& a43,
-                                              float& a5) {
+__device__ __forceinline__ void accum6<float, true>(float sa, float g0, float2 zz, float& a0, float2& a21,
+                                                    float2& a43, float& a5) {
   const float s0 = sa * g0;
   const float2 t = __fmul2_rn(zz, make_float2(sa, sa));
   a21 = __ffma2_rn(t, zz, a21);
@@ -685,7 +695,7 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
     }
     fft_pencil<T, N, E, +1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
-    for (int r = 0; r < E; ++r) accum6<T>(sa, zB[r].x, z[r], a0[r], a21[r], a43[r], a5[r]);
+    for (int r = 0; r < E; ++r) accum6<T, (sizeof(T) == 4 && N <= 256)>(sa, zB[r].x, z[r], a0[r], a21[r], a43[r], a5[r]);
     if (two) {  // uniform across the CTA
       const T sb = sigma[a + 1];
 #pragma unroll
@@ -695,7 +705,7 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
       }
       fft_pencil<T, N, E, +1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
-      for (int r = 0; r < E; ++r) accum6<T>(sb, zB[r].y, z[r], a0[r], a21[r], a43[r], a5[r]);
+      for (int r = 0; r < E; ++r) accum6<T, (sizeof(T) == 4 && N <= 256)>(sb, zB[r].y, z[r], a0[r], a21[r], a43[r], a5[r]);
     }
     __syncthreads();  // stage s fully read before it is refilled
   }

@@ -100,7 +100,7 @@ struct OpsT {
   static cudaError_t p2_n(const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
                           const void* tw, int variant, cudaStream_t st) {
     using SH = Shape<T, N>;
-    using AL = AltStrided<T, N>;
+    using AL = AltStrided2<T, N>;
     if constexpr (AL::exists) {
       if (variant & 4) return p2_v<N, AL::E, AL::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
     }
