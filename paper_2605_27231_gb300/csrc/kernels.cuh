@@ -586,6 +586,44 @@ __device__ __forceinline__ cx<T> herm_grad_r(const cx<T>* row, int j, int r, T f
   return mk<T>(-n * x.y, n * x.x);
 }
 
+// The same values by a run-time test on k = j + r P.  At N = 512 this form measured faster in the radix-16 last
+// pass (the specialised form above costs registers there, where the kernel already spills).
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_plain_k(const cx<T>* row, int j, int r) {
+  constexpr int H = N / 2;
+  const int k = j + r * (N / E);
+  if (k == 0) return mk<T>(row[0].x, (T)0);
+  if (k == H) return mk<T>(row[0].y, (T)0);
+  if (k < H) return row[k];
+  return conjg<T>(row[N - k]);
+}
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_grad_k(const cx<T>* row, int j, int r) {
+  constexpr int H = N / 2;
+  const int k = j + r * (N / E);
+  if (k == 0 || k == H) return mk<T>((T)0, (T)0);
+  cx<T> x;
+  T n;
+  if (k < H) {
+    x = row[k];
+    n = (T)k;
+  } else {
+    x = conjg<T>(row[N - k]);
+    n = (T)(k - N);
+  }
+  return mk<T>(-n * x.y, n * x.x);
+}
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> row_plain(const cx<T>* row, int j, int r) {
+  if constexpr (N <= 256) return herm_plain_r<T, N, E>(row, j, r);
+  else return herm_plain_k<T, N, E>(row, j, r);
+}
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> row_grad(const cx<T>* row, int j, int r, T fj) {
+  if constexpr (N <= 256) return herm_grad_r<T, N, E>(row, j, r, fj);
+  else return herm_grad_k<T, N, E>(row, j, r);
+}
+
 // One term's contribution sigma g_i g_j to the six product components at one point, with zz = (g2, g1):
 // a0 = s_00, a21 = (s_22, s_11), a43 = (s_02, s_01), a5 = s_12.  PAIRED (FP32, N <= 256) uses paired (FP32x2)
 // multiply-adds; at N = 512 their aligned register pairs made the radix-16 last pass spill, so it stays scalar.
@@ -682,15 +720,15 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
     cx<T> zB[E], z[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      const cx<T> g0 = herm_plain_r<T, N, E>(w20, j, r);
-      const cx<T> g0b = two ? herm_plain_r<T, N, E>(w21, j, r) : mk<T>((T)0, (T)0);
+      const cx<T> g0 = row_plain<T, N, E>(w20, j, r);
+      const cx<T> g0b = two ? row_plain<T, N, E>(w21, j, r) : mk<T>((T)0, (T)0);
       zB[r] = mk<T>(g0.x - g0b.y, g0.y + g0b.x);
     }
     fft_pencil<T, N, E, +1, Lay, Sync>(zB, j, L, tw, Sync());
     const T sa = sigma[a];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      const cx<T> g2 = herm_grad_r<T, N, E>(wb0, j, r, fj), g1 = herm_plain_r<T, N, E>(w10, j, r);
+      const cx<T> g2 = row_grad<T, N, E>(wb0, j, r, fj), g1 = row_plain<T, N, E>(w10, j, r);
       z[r] = mk<T>(g2.x - g1.y, g2.y + g1.x);
     }
     fft_pencil<T, N, E, +1, Lay, Sync>(z, j, L, tw, Sync());
@@ -700,7 +738,7 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
       const T sb = sigma[a + 1];
 #pragma unroll
       for (int r = 0; r < E; ++r) {
-        const cx<T> h2 = herm_grad_r<T, N, E>(wb1, j, r, fj), h1 = herm_plain_r<T, N, E>(w11, j, r);
+        const cx<T> h2 = row_grad<T, N, E>(wb1, j, r, fj), h1 = row_plain<T, N, E>(w11, j, r);
         z[r] = mk<T>(h2.x - h1.y, h2.y + h1.x);
       }
       fft_pencil<T, N, E, +1, Lay, Sync>(z, j, L, tw, Sync());
