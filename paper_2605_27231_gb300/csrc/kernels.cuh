@@ -98,14 +98,6 @@ template <typename T, int N> struct AltStrided2 {
   static constexpr int TC = N == 512 ? 16 : AltStrided<T, N>::TC;
 };
 
-// Exchange layout of the first strided pass: with the Phi~ tile in shared memory (TILE) one buffer is used.
-template <typename T, int N, int TC, int E, bool TILE> struct P1Lay {
-  using type = ColLayout<T, N, TC, E, (TILE || E >= 32)>;
-};
-// The first pass keeps its Phi~ tile in shared memory by default at N = 512 (FP32), where the register tile
-// (172 registers) would leave one CTA per SM.
-template <typename T, int N> struct P1Tile { static constexpr bool value = sizeof(T) == 4 && N == 512; };
-
 template <int P> struct RowSync { using type = SyncWarp; };
 template <> struct RowSync<64> { using type = SyncBlock; };
 template <> struct RowSync<128> { using type = SyncBlock; };
@@ -385,21 +377,17 @@ __global__ void k_reduce_mean(const double* __restrict__ part, int nblk, double*
 // P1: first inverse pass along axis 0 for a tile of TC packed columns at fixed k1.
 //   V_a(n) = phi_a(cell(|n|^2)) Phi~(n)          (column 0: V(k2=0) + i V(k2=H), each with its own cell)
 //   Ta_a = IDFT_0[V_a],  Tb_a = IDFT_0[i n0^D V_a]
-// TILE: the Phi~ tile and its cells live in shared memory instead of registers, with a single exchange buffer,
-// so that two CTAs fit per SM where the register tile would allow only one (N = 512).
-template <typename T, int N, int E_ = Shape<T, N>::ES, int TC_ = Shape<T, N>::TC, bool TILE = false>
-__global__ void __launch_bounds__(256, (TILE || (sizeof(T) == 4 && E_ <= 16 && N <= 256)) ? 2 : 1) k_p1(const cx<T>* __restrict__ phi, cx<T>* __restrict__ Ta,
-                                                          cx<T>* __restrict__ Tb, const int16_t* __restrict__ lut,
-                                                          const T* __restrict__ phitab, int nm1, int alpha0, int nb,
-                                                          const cx<T>* __restrict__ tw) {
+template <typename T, int N, int E_ = Shape<T, N>::ES, int TC_ = Shape<T, N>::TC>
+__global__ void __launch_bounds__(256) k_p1(const cx<T>* __restrict__ phi, cx<T>* __restrict__ Ta,
+                                            cx<T>* __restrict__ Tb, const int16_t* __restrict__ lut,
+                                            const T* __restrict__ phitab, int nm1, int alpha0, int nb,
+                                            const cx<T>* __restrict__ tw) {
   constexpr int E = E_, P = N / E_, TC = TC_, H = N / 2, NH = H + 1;
-  using Lay = typename P1Lay<T, N, TC, E, TILE>::type;
+  using Lay = StridedLay<T, N, TC, E>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cx<T>* sm_ph = reinterpret_cast<cx<T>*>(smraw) + Lay::SIZE;    // TILE: N * TC values
-  cx<T>* sm_nyq = sm_ph + (TILE ? N * TC : 0);                    // N values (column 0 only)
-  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);                // N cells
-  T* sm_tab = reinterpret_cast<T*>(sm_cn + N);                    // nb * nm1
-  int16_t* sm_cell = reinterpret_cast<int16_t*>(sm_tab + nb * nm1);  // TILE: N * TC cells
+  cx<T>* sm_nyq = reinterpret_cast<cx<T>*>(smraw) + Lay::SIZE;  // N values (column 0 only)
+  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);              // N cells
+  T* sm_tab = reinterpret_cast<T*>(sm_cn + N);                  // nb * nm1
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
   const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int cc = blockIdx.x * TC + c;
@@ -415,21 +403,14 @@ __global__ void __launch_bounds__(256, (TILE || (sizeof(T) == 4 && E_ <= 16 && N
       sm_cn[k0] = lut[n0 * n0 + n1 * n1 + H * H];
     }
   }
-  cx<T> ph[TILE ? 1 : E];
-  int cell[TILE ? 1 : E];
+  cx<T> ph[E];
+  int cell[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) {
     const int k0 = j + r * P;
     const int n0 = wrapn(k0, N);
-    const cx<T> x = pb[(long)k0 * N * NH + cc];
-    const int ce = lut[n0 * n0 + n1 * n1 + cc * cc];
-    if constexpr (TILE) {
-      sm_ph[k0 * TC + c] = x;
-      sm_cell[k0 * TC + c] = (int16_t)ce;
-    } else {
-      ph[r] = x;
-      cell[r] = ce;
-    }
+    ph[r] = pb[(long)k0 * N * NH + cc];
+    cell[r] = lut[n0 * n0 + n1 * n1 + cc * cc];
   }
   __syncthreads();
   const long fstride = (long)N * N * H;  // one field
@@ -443,18 +424,10 @@ __global__ void __launch_bounds__(256, (TILE || (sizeof(T) == 4 && E_ <= 16 && N
       cx<T> v[E];
 #pragma unroll
       for (int r = 0; r < E; ++r) {
-        const int k0 = j + r * P;
-        cx<T> p0;
-        T f;
-        if constexpr (TILE) {
-          p0 = sm_ph[k0 * TC + c];
-          f = tab[sm_cell[k0 * TC + c]];
-        } else {
-          p0 = ph[r];
-          f = tab[cell[r]];
-        }
-        cx<T> x = mk<T>(f * p0.x, f * p0.y);
+        const T f = tab[cell[r]];
+        cx<T> x = mk<T>(f * ph[r].x, f * ph[r].y);
         if (cc == 0) {
+          const int k0 = j + r * P;
           const T fn = tab[sm_cn[k0]];
           const cx<T> yn = sm_nyq[k0];
           x = mk<T>(x.x - fn * yn.y, x.y + fn * yn.x);

@@ -64,13 +64,11 @@ struct OpsT {
     return cudaGetLastError();
   }
   // ------------------------------------------------------------ hot path
-  template <int N, int E, int TC, bool TILE = false>
+  template <int N, int E, int TC>
   static cudaError_t p1_v(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
                           int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
-    using Lay = typename P1Lay<T, N, TC, E, TILE>::type;
-    const size_t sm = (size_t)Lay::SIZE * sizeof(C) + (TILE ? (size_t)N * TC * (sizeof(C) + sizeof(int16_t)) : 0) +
-                      N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
-    auto k = k_p1<T, N, E, TC, TILE>;
+    const size_t sm = strided_bytes<N, TC, E>() + N * sizeof(C) + N * sizeof(int) + (size_t)nb * nm1 * sizeof(T);
+    auto k = k_p1<T, N, E, TC>;
     SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
     dim3 grid((N / 2) / TC, N, batch);
     k<<<grid, TC * (N / E), sm, st>>>((const C*)phi, (C*)Ta, (C*)Tb, lut, (const T*)phitab, nm1, alpha0, nb,
@@ -86,7 +84,7 @@ struct OpsT {
       if (variant & 1)
         return p1_v<N, AL::E, AL::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
     }
-    return p1_v<N, SH::ES, SH::TC, P1Tile<T, N>::value>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
+    return p1_v<N, SH::ES, SH::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
   }
   template <int N, int E, int TC>
   static cudaError_t p2_v(const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
