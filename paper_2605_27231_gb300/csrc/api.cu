@@ -429,6 +429,9 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
   p->L = L;
   p->opts = o;
   p->B = auto_alpha_batch(o);
+  // Untuned default: the radices the autotuner chose on GB300 at usr256 and broad512 (radix-16 last pass from
+  // 128^3; at 512^3 also the 512-specific strided passes).  sigw_plan_autotune or the table may override it.
+  p->variant = o.precision == 32 ? (N == 512 ? 7 : (N >= 128 ? 2 : 0)) : 0;
   std::string e;
   if (!sigw::build_decomposition(params_of(o), &p->dec, &e)) {
     delete p;
