@@ -873,14 +873,17 @@ __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_
   }
   const int cc = cc0 + c;
   const bool valid = cc < ncp && n1 * n1 + cc * cc <= rmax;
+  // all six components are loaded before the first transform, so their latencies overlap (a barrier inside a
+  // transform would otherwise hold back the loads of the next component)
   cx<T> X[6][E];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     const cx<T>* in = F2 + (((long)b * 6 + q) * N * nk1 + k1i) * (long)ncp + (valid ? cc : 0);
 #pragma unroll
     for (int r = 0; r < E; ++r) X[q][r] = valid ? in[(long)(j + r * P) * nk1 * ncp] : mk<T>((T)0, (T)0);
-    fft_pencil<T, N, E, -1, Lay, SyncBlock>(X[q], j, L, tw, SyncBlock());
   }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) fft_pencil<T, N, E, -1, Lay, SyncBlock>(X[q], j, L, tw, SyncBlock());
   double acc = 0.0;
   if (valid) {
     const int n2 = cc;
