@@ -37,7 +37,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # proportion to the term-realisations of a launch, so the traffic of a bench launch is the algorithmic bytes of
 # that launch times the captured ratio.  Valid only while the kernel source is unchanged since the capture.
 NCU_TRAFFIC_256 = {
-    "p1_inv_axis0_filter": (0.068532e9 + 1.281052e9, 0.0676e9 + 20 * 67.108864e6),
+    "p1_inv_axis0_filter": (0.068546e9 + 1.281282e9, 0.0676e9 + 20 * 67.108864e6),
     "p2_inv_axis1": (1.073817e9 + 1.553402e9, 40 * 67.108864e6),
     "p3_inv_axis2_product_fwd_axis2": (2.013373e9 + 0.026424e9, 30 * 67.108864e6 + 6 * 65536 * 2 * 8),
 }
