@@ -279,6 +279,8 @@ def serving_run(args):
     sizes = (64, 128, 256)
     srv = sigw.Server(args.serve_budget_gb * 1e9, max_slots=args.serve_slots, max_batch=args.serve_batch,
                       precision=32)
+    if args.serve_express > 0:
+        srv.set_express(args.serve_express, args.serve_express_max_n)
     try:
         service = {}
         for N in sizes:  # warm plans, then time one request alone
@@ -312,6 +314,8 @@ def serving_run(args):
             "p50_latency_s": pct(allv, 50), "p99_latency_s": pct(allv, 99),
             "per_size": {str(N): {"n": len(v), "p50_s": pct(v, 50), "p99_s": pct(v, 99)} for N, v in lat.items()},
             "slots": args.serve_slots, "max_batch": args.serve_batch, "batches": st["batches"],
+            "express_slots": args.serve_express, "express_max_n": args.serve_express_max_n,
+            "express_batches": st["express_batches"],
             "hbm_peak_gb": st["hbm_peak"] / 1e9, "budget_gb": args.serve_budget_gb,
             "mix": "N uniform over {64,128,256}; f_NL ~ U[-5,20]; sigma ~ U[0.1,1]; map uniform over "
                    "{gauss, local, usr}; Poisson arrivals, seed 7; FP32"}
@@ -443,6 +447,8 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-batch", type=int, default=4)
+    ap.add_argument("--serve-express", type=int, default=1, help="express slots for small lattices (0: none)")
+    ap.add_argument("--serve-express-max-n", type=int, default=128)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -203,6 +203,7 @@ const char* sigw_strerror(sigw_status s);
 typedef struct sigw_server_stats {
   uint64_t submitted, completed, failed, queued, batches, plans_created, plans_evicted, plans_resident;
   size_t hbm_in_use, hbm_peak, hbm_budget;
+  uint64_t express_batches; /* batches run by express slots */
 } sigw_server_stats;
 
 /* opts: plan options of every plan (NULL: defaults; max_batch is the per-batch cap).  Errors: SIGW_EINVAL. */
@@ -222,6 +223,12 @@ sigw_status sigw_poll(sigw_server srv, uint64_t ticket, double* omega, double* l
 sigw_status sigw_wait(sigw_server srv, uint64_t ticket, double timeout_s, double* omega, double* latency_s);
 
 sigw_status sigw_server_stats_read(sigw_server srv, sigw_server_stats* out);
+
+/* Adds `slots` express worker slots (once per server) that take only requests with N <= max_N, in arrival order,
+ * under the same pool, budget and admission rule; small requests then need not wait for a general slot held by
+ * batches of large lattices (their kernels also run on higher-priority streams).  Errors: SIGW_EINVAL
+ * (slots not in [1, 16], max_N not in [8, 512]), SIGW_ESTATE (already set). */
+sigw_status sigw_server_set_express(sigw_server srv, int slots, int max_N);
 
 /* Finishes running batches, drops queued requests, frees every plan. */
 sigw_status sigw_server_destroy(sigw_server srv);

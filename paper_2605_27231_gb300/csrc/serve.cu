@@ -11,6 +11,9 @@
 // queue cannot starve.  A request whose plan alone exceeds the budget is refused at submission (SIGW_EBUSY).
 // Plans run on streams whose priority falls with the lattice size (smaller lattices first), so short requests
 // are not held behind the thread blocks of long ones when they share the device.
+// Express slots (sigw_server_set_express) are extra workers that take only requests of small lattices (N at most
+// a given size), so short requests do not wait behind batches of large ones for a free general slot; they use
+// the same pool, budget and admission rule, applied among the requests they may take.
 // Latency of a request = completion time - submission time.
 #include <cuda_runtime.h>
 
@@ -72,7 +75,9 @@ struct sigw_server_s {
   bool stop = false;
   uint64_t next_ticket = 1, tick = 0;
   uint64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_batches = 0, n_plans_created = 0, n_evicted = 0;
+  uint64_t n_express_batches = 0;
   size_t peak_in_use = 0;
+  int express_slots = 0;
 };
 
 namespace {
@@ -145,24 +150,27 @@ void finish(sigw_server_s* s, std::vector<Req*>& batch, sigw_status st, const do
   }
 }
 
-void worker_main(sigw_server_s* s) {
+// max_N = 0: a general slot (any request); otherwise an express slot (requests with N <= max_N only).
+void worker_main(sigw_server_s* s, int max_N) {
   cudaSetDevice(s->dev);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     if (s->stop) break;
-    // pick the oldest admissible request
+    // pick the oldest admissible request this slot may take
     PoolPlan* use = nullptr;
     Req* head = nullptr;
     bool create = false;
     size_t need = 0;
     std::vector<Doomed> destroy;
+    bool first = true;
     for (size_t qi = 0; qi < s->queue.size(); ++qi) {
       Req* r = s->queue[qi];
+      if (max_N > 0 && r->N > max_N) continue;
       if ((use = idle_plan(s, r->N, r->L))) {
         head = r;
         break;
       }
-      if (qi == 0) {  // only the head may allocate
+      if (first) {  // only the oldest request this slot may take may allocate
         need = footprint_of(s, r->N);
         if (make_room(s, need, &destroy)) {
           head = r;
@@ -170,6 +178,7 @@ void worker_main(sigw_server_s* s) {
           break;
         }
       }
+      first = false;
     }
     if (!head) {
       if (!destroy.empty()) {
@@ -203,6 +212,7 @@ void worker_main(sigw_server_s* s) {
       }
     }
     s->n_batches++;
+    if (max_N > 0) s->n_express_batches++;
     lk.unlock();
     destroy_all(destroy);
     sigw_status st = SIGW_OK;
@@ -275,7 +285,7 @@ sigw_status sigw_server_create(size_t hbm_budget_bytes, int max_slots, const sig
     delete s;
     return SIGW_ECUDA;
   }
-  for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker_main, s);
+  for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker_main, s, 0);
   *out = s;
   return SIGW_OK;
 }
@@ -301,6 +311,15 @@ sigw_status sigw_submit(sigw_server s, int N, double L, const sigw_pzeta* pz, co
   s->n_submitted++;
   *ticket = r->ticket;
   s->cv.notify_all();
+  return SIGW_OK;
+}
+
+sigw_status sigw_server_set_express(sigw_server s, int slots, int max_N) {
+  if (!s || slots < 1 || slots > 16 || max_N < 8 || max_N > 512) return SIGW_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->express_slots > 0 || s->stop) return SIGW_ESTATE;
+  s->express_slots = slots;
+  for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_main, s, max_N);
   return SIGW_OK;
 }
 
@@ -349,6 +368,7 @@ sigw_status sigw_server_stats_read(sigw_server s, sigw_server_stats* out) {
   out->hbm_in_use = s->in_use;
   out->hbm_peak = s->peak_in_use;
   out->hbm_budget = s->budget;
+  out->express_batches = s->n_express_batches;
   return SIGW_OK;
 }
 

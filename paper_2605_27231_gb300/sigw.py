@@ -59,7 +59,7 @@ class Profile(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "queued", "batches", "plans_created",
                                           "plans_evicted", "plans_resident")] + \
-               [(n, C.c_size_t) for n in ("hbm_in_use", "hbm_peak", "hbm_budget")]
+               [(n, C.c_size_t) for n in ("hbm_in_use", "hbm_peak", "hbm_budget")] + [("express_batches", C.c_uint64)]
 
 
 _lib = None
@@ -98,6 +98,7 @@ def lib():
         "sigw_fft3d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P]),
         "sigw_generate_batch": (C.c_int, [P, C.POINTER(PZeta), C.POINTER(NGMap), C.POINTER(C.c_uint64), C.c_int, _i64]),
         "sigw_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(Opts), C.POINTER(P)]),
+        "sigw_server_set_express": (C.c_int, [P, C.c_int, C.c_int]),
         "sigw_submit": (C.c_int, [P, C.c_int, C.c_double, C.POINTER(PZeta), C.POINTER(NGMap), C.c_uint64,
                                   C.POINTER(C.c_uint64)]),
         "sigw_poll": (C.c_int, [P, C.c_uint64, _dbl, _dbl]),
@@ -367,6 +368,10 @@ class Server:
                "sigw_server_create")
         self._h = h
         self._N = {}
+
+    def set_express(self, slots, max_N):
+        """sigw_server_set_express: extra slots for requests with N <= max_N."""
+        _check(lib().sigw_server_set_express(self._h, slots, max_N), None, "sigw_server_set_express")
 
     def submit(self, spec):
         t = C.c_uint64()

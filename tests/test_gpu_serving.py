@@ -88,3 +88,24 @@ def test_server_wait_timeout_then_result(lib):
         assert np.all(np.isfinite(om)) and lat > 0
         with pytest.raises(lib.SigwError):
             srv.poll(t)  # ticket consumed
+
+
+def test_express_slot_serves_small_requests_beside_a_large_batch(lib):
+    """With one general slot busy on a 128^3 request, the express slot (N <= 32) takes the small requests that
+    arrive behind it; every result still equals its single-plan value."""
+    big = _spec(128, "local", 300, F=2.0)
+    small = [_spec(16, "gauss", 301), _spec(32, "usr", 302), _spec(16, "local", 303, F=1.0)]
+    with lib.Server(40e9, max_slots=1, max_batch=2, precision=32) as srv:
+        srv.set_express(1, 32)
+        with pytest.raises(lib.SigwError) as e:
+            srv.set_express(1, 32)
+        assert e.value.status == lib.ESTATE
+        tb = srv.submit(big)
+        ts = [srv.submit(s) for s in small]
+        res_small = [srv.wait(t, timeout_s=300) for t in ts]
+        om_big, _ = srv.wait(tb, timeout_s=300)
+        st = srv.stats()
+    assert st["completed"] == 4 and st["failed"] == 0 and st["express_batches"] >= 1
+    np.testing.assert_allclose(om_big, _alone(lib, big), rtol=1e-4)
+    for s, (om, lat) in zip(small, res_small):
+        np.testing.assert_allclose(om, _alone(lib, s), rtol=1e-4)
