@@ -241,12 +241,9 @@ def run_ours(args):
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == 32 else "f64",
             "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
-            "config": {"workload": args.workload, "N": spec.N, "L": spec.L, "A": spec.A, "sigma": spec.sigma,
-                       "kstar_over_kf": round(spec.kstar * spec.L / (2 * 3.141592653589793), 6), "map": spec.kind,
-                       "seeds_per_step": batch, "shells": n_sh, "n_alpha": args.n_alpha, "n_modes": 200,
-                       "l2": "inputs larger than L2 (%.1f GB device working set per step)" % (sigw.footprint(
-                           spec.N, sigw.default_opts(max_batch=batch)) / 1e9),
-                       "parallelism": "replicas, seeds sharded across ranks", "autotuned": tuned},
+            "config": dict(workload_config(args, spec),
+                           l2="inputs larger than L2 (%.1f GB device working set per step)" % (sigw.footprint(
+                               spec.N, sigw.default_opts(max_batch=batch)) / 1e9), autotuned=tuned),
             "e2e": {"value": e2e_value, "unit": "spectra/s", "h2d_bytes_per_step": io["h2d_bytes"] / args.steps,
                     "d2h_bytes_per_step": io["d2h_bytes"] / args.steps},
             "gpu_launches": launches,
@@ -401,6 +398,14 @@ def oracle_sample(spec, n_terms):
             "seconds_per_spectrum": per_spec}
 
 
+def workload_config(args, spec):
+    """The workload keys of the JSON line, shared by both arms."""
+    return {"workload": args.workload, "N": spec.N, "L": spec.L, "A": spec.A, "sigma": spec.sigma,
+            "kstar_over_kf": round(spec.kstar * spec.L / (2 * 3.141592653589793), 6), "map": spec.kind,
+            "seeds_per_step": args.batch, "shells": spec.N // 2, "n_alpha": args.n_alpha, "n_modes": 200,
+            "parallelism": "replicas, seeds sharded across ranks"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -418,7 +423,7 @@ def run_reference(args):
             "value": v, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / (args.warmup + args.steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
-            "config": {"workload": args.workload, "N": spec.N},
+            "config": workload_config(args, spec),
             "cpu_baseline": {"value": v, "unit": "spectra/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
