@@ -193,7 +193,10 @@ template <typename T, int N, int TC, int E, bool ONE = false> struct ColLayout {
   static constexpr bool SINGLE = ONE;
   static constexpr int PER_PHASE = 128 / (int)sizeof(cx<T>);
   static constexpr int G0 = PER_PHASE / TC;
-  static constexpr int G = G0 < 1 ? 1 : G0;
+  // (p + p/E) mod G permutes each aligned group of G positions only while G <= E (p/E is then constant in the
+  // group); a larger G would make two rows collide.
+  static constexpr int G1 = G0 < 1 ? 1 : G0;
+  static constexpr int G = G1 > E ? E : G1;
   static constexpr int BUF = N * TC;
   static constexpr int SIZE = ONE ? BUF : 2 * BUF;  // elements for all TC pencils
   cx<T>* base;  // shared by the TC pencils of the CTA
