@@ -67,11 +67,12 @@ template <typename T, int N> struct Shape {
   static constexpr int PR = N / ER;
   static constexpr int RPC0 = 256 / PR;
   static constexpr int RPC = RPC0 > (N * N / 2) ? (N * N / 2) : RPC0;
-  // forward-a0 + TT pass: one group of 128 threads per component (six groups per CTA), TC3 columns per CTA
+  // forward-a0 + TT pass keeps six spectra per thread: fewer values per thread
   static constexpr int E3 = (sizeof(T) == 4) ? (N >= 16 ? 8 : 4) : 4;
   static constexpr int P3 = N / E3;
-  static constexpr int TC3 = 128 / P3 < 1 ? 1 : 128 / P3;
-  static constexpr int F3_THREADS = 6 * TC3 * P3;
+  static constexpr int TC3_0 = 256 / P3;
+  static constexpr int TC3_1 = TC3_0 < 1 ? 1 : (TC3_0 > 8 ? 8 : TC3_0);
+  static constexpr int TC3 = TC3_1 * P3 < 32 ? 32 / P3 : TC3_1;  // whole warps (the partial sum uses shuffles)
 };
 
 // Alternative radix of the strided inverse passes (variant bit 1 for the first pass; the second pass uses
@@ -848,20 +849,16 @@ __device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2
 // Xj[b][0] = e^+ : S and Xj[b][1] = -i e^x : S (both Hermitian in this basis away from the Nyquist shell),
 // [b][f][k0][k1][k2], k2 = 0..N/2; every other entry is left as it is (zero).
 template <typename T, int N>
-__global__ void __launch_bounds__(Shape<T, N>::F3_THREADS, 1) k_f3(const cx<T>* __restrict__ F2, int n_c, int n1lo,
-                                                                  int nk1, double* __restrict__ partial,
-                                                                  long pbstride, const cx<T>* __restrict__ tw,
-                                                                  cx<T>* __restrict__ Xj) {
+__global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_c, int n1lo, int nk1,
+                                            double* __restrict__ partial, long pbstride,
+                                            const cx<T>* __restrict__ tw, cx<T>* __restrict__ Xj) {
   using SH = Shape<T, N>;
-  constexpr int E = SH::E3, P = SH::P3, TC = SH::TC3, H = N / 2, G = TC * P;  // G threads per component
+  constexpr int E = SH::E3, P = SH::P3, TC = SH::TC3, H = N / 2;
   using Lay = ColLayout<T, N, TC, E>;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
-  // the six components are transformed side by side, one thread group each (threads q G .. q G + G - 1)
-  const int q = threadIdx.x / G, t = threadIdx.x % G;
-  const int c = t % TC, j = t / TC;
-  cx<T>* region = reinterpret_cast<cx<T>*>(smraw) + q * Lay::SIZE;
-  const Lay L{region, c};
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  const Lay L{reinterpret_cast<cx<T>*>(smraw), c};
   const int ncp = n_c + 1;
   const int k1i = blockIdx.y;
   const int n1 = n1lo + k1i;
@@ -874,55 +871,53 @@ __global__ void __launch_bounds__(Shape<T, N>::F3_THREADS, 1) k_f3(const cx<T>* 
     if (threadIdx.x == 0) partial[(long)b * pbstride + blk] = 0.0;
     return;
   }
-  {
-    const int cc = cc0 + c;
-    const bool valid = cc < ncp && n1 * n1 + cc * cc <= rmax;
+  const int cc = cc0 + c;
+  const bool valid = cc < ncp && n1 * n1 + cc * cc <= rmax;
+  // all six components are loaded before the first transform, so their latencies overlap (a barrier inside a
+  // transform would otherwise hold back the loads of the next component)
+  cx<T> X[6][E];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
     const cx<T>* in = F2 + (((long)b * 6 + q) * N * nk1 + k1i) * (long)ncp + (valid ? cc : 0);
-    cx<T> X[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) X[r] = valid ? in[(long)(j + r * P) * nk1 * ncp] : mk<T>((T)0, (T)0);
-    fft_pencil<T, N, E, -1, Lay, SyncBlock>(X, j, L, tw, SyncBlock());
-    // S[q][k0][c] in the group's (now free) exchange region
-#pragma unroll
-    for (int r = 0; r < E; ++r) region[(j + r * P) * TC + c] = X[r];
+    for (int r = 0; r < E; ++r) X[q][r] = valid ? in[(long)(j + r * P) * nk1 * ncp] : mk<T>((T)0, (T)0);
   }
-  __syncthreads();
-  const cx<T>* S6 = reinterpret_cast<const cx<T>*>(smraw);
-  double acc = 0.0;
-  for (int m = threadIdx.x; m < N * TC; m += blockDim.x) {  // modes (k0, column) of the tile
-    const int k0 = m / TC, cm = m % TC;
-    const int n2 = cc0 + cm;
-    if (n2 >= ncp) continue;
-    const int n0 = wrapn(k0, N);
-    const int msq = n0 * n0 + n1 * n1 + n2 * n2;
-    if (msq < rmin || msq > rmax) continue;
-    double2 S[6];
 #pragma unroll
-    for (int qq = 0; qq < 6; ++qq) {
-      const cx<T> v = S6[qq * Lay::SIZE + k0 * TC + cm];
-      S[qq] = make_double2((double)v.x, (double)v.y);
-    }
-    double2 ap, ax;
-    tt_amp(n0, n1, n2, S, ap, ax);
-    acc += ap.x * ap.x + ap.y * ap.y + ax.x * ax.x + ax.y * ax.y;
-    if (Xj) {
-      constexpr long NNH = (long)N * N * (H + 1);
-      const long o = ((long)b * 2 * N + k0) * N * (H + 1) + (long)((n1 + N) % N) * (H + 1) + n2;
-      Xj[o] = mk<T>((T)ap.x, (T)ap.y);
-      Xj[o + NNH] = mk<T>((T)ax.y, (T)-ax.x);
-    }
-    if (n2 > 0 && n2 < H) {
-      const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
-      acc += tt_power(p0, p1, -n2, S);
+  for (int q = 0; q < 6; ++q) fft_pencil<T, N, E, -1, Lay, SyncBlock>(X[q], j, L, tw, SyncBlock());
+  double acc = 0.0;
+  if (valid) {
+    const int n2 = cc;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int n0 = wrapn(j + r * P, N);
+      const int msq = n0 * n0 + n1 * n1 + n2 * n2;
+      if (msq >= rmin && msq <= rmax) {
+        double2 S[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) S[q] = make_double2((double)X[q][r].x, (double)X[q][r].y);
+        double2 ap, ax;
+        tt_amp(n0, n1, n2, S, ap, ax);
+        acc += ap.x * ap.x + ap.y * ap.y + ax.x * ax.x + ax.y * ax.y;
+        if (Xj) {
+          constexpr long NNH = (long)N * N * (H + 1);
+          const long o = ((long)b * 2 * N + (j + r * P)) * N * (H + 1) + (long)((n1 + N) % N) * (H + 1) + n2;
+          Xj[o] = mk<T>((T)ap.x, (T)ap.y);
+          Xj[o + NNH] = mk<T>((T)ax.y, (T)-ax.x);
+        }
+        if (n2 > 0 && n2 < H) {
+          const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
+          acc += tt_power(p0, p1, -n2, S);
+        }
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
-    partial[(long)b * pbstride + blk] = tot;
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    partial[(long)b * pbstride + blk] = t;
   }
 }
 

@@ -150,13 +150,13 @@ struct OpsT {
   static cudaError_t f3_n(const void* F2, int n_c, double* partial, long pbs, int batch, const void* tw,
                           cudaStream_t st, void* Xj) {
     using SH = Shape<T, N>;
-    const size_t sm = 6 * col_bytes<N, SH::TC3, SH::E3>();
+    const size_t sm = col_bytes<N, SH::TC3, SH::E3>();
     auto k = k_f3<T, N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     int lo, nk1;
     n1_range(N, n_c, &lo, &nk1);
     dim3 grid((n_c + 1 + SH::TC3 - 1) / SH::TC3, nk1, batch);
-    k<<<grid, SH::F3_THREADS, sm, st>>>((const C*)F2, n_c, lo, nk1, partial, pbs, (const C*)tw, (C*)Xj);
+    k<<<grid, SH::TC3 * SH::P3, sm, st>>>((const C*)F2, n_c, lo, nk1, partial, pbs, (const C*)tw, (C*)Xj);
     return cudaGetLastError();
   }
   template <int N>
