@@ -5,9 +5,9 @@ quotes from Witkowski:
   Omega(k) = int_0^1 dq int_1^inf ds T(q,s) Delta^2(k (s+q)/2) Delta^2(k (s-q)/2)
   T(q,s)   = 12 (q^2+s^2-6)^4 (q^2-1)^2 (s^2-1)^2 / (s^2-q^2)^8
              * [ (ln|(3-q^2)/(3-s^2)| + 2(s^2-q^2)/(q^2+s^2-6))^2 + pi^2 Theta(s - sqrt3) ]
-evaluated by adaptive quadrature in FP64, the s range split at the integrable
-log singularity s = sqrt3 and cut where the integrand's Delta^2 factors fall
-below 1e-30 of their peak.
+evaluated by adaptive quadrature in FP64 over q and t = ln s, the t range split at
+the integrable log singularity s = sqrt3 and at the peak s = 2 k*/k, and cut where
+the integrand's Delta^2 factors fall below 1e-30 of their peak.
 
 Also the paper's box-size rule (Sec. sec_numerical): L = pi N / k_max,
 k_max = 3 max(k, k_bar), with k_bar the (1 - eps) quantile of int Delta^2 dln k.
@@ -31,23 +31,29 @@ def T_kernel(q, s):
 
 
 def omega_gauss(k, A, sigma, kstar):
-    """Eq. eq_semi_anal for the log-normal Delta^2 of Eq. eq_lognormal."""
+    """Eq. eq_semi_anal for the log-normal Delta^2 of Eq. eq_lognormal.
+
+    The s integral runs over t = ln s: the Delta^2 factors put the integrand's weight near s = 2 k*/k, a
+    feature of relative width ~sigma that, on a linear s axis, would sit in an interval up to ~1e5 long for a
+    broad peak (sigma = 1), where adaptive quadrature does not resolve it.  Breakpoints at s = sqrt3 (the
+    integrable log singularity) and at the peak s = 2 k*/k."""
     # support of Delta^2(k (s+q)/2): |ln(k (s+q)/(2 k*))| < sigma sqrt(2 ln 1e30)
     width = sigma * np.sqrt(2.0 * np.log(1e30))
-    smax = 2.0 * kstar * np.exp(width) / k + 1.0
+    tmax = np.log(2.0 * kstar * np.exp(width) / k + 1.0)
+    tpk = np.log(2.0 * kstar / k)
+    pts = sorted({0.0, np.log(SQRT3), tmax} | ({tpk} if 0.0 < tpk < tmax else set()))
 
     def inner(q):
-        f = lambda s: T_kernel(q, s) * delta2_lognormal(k * (s + q) / 2.0, A, sigma, kstar) \
-            * delta2_lognormal(k * (s - q) / 2.0, A, sigma, kstar)
-        pts = [1.0, SQRT3, max(SQRT3 + 1e-9, smax)]
+        def f(t):
+            s = np.exp(t)
+            return s * T_kernel(q, s) * delta2_lognormal(k * (s + q) / 2.0, A, sigma, kstar) \
+                * delta2_lognormal(k * (s - q) / 2.0, A, sigma, kstar)
         tot = 0.0
         for a, b in zip(pts[:-1], pts[1:]):
-            if b > a:
-                # log-spaced breakpoints where the peak factor lives
-                tot += integrate.quad(f, a, b, limit=400, epsabs=0.0, epsrel=1e-10)[0]
+            tot += integrate.quad(f, a, b, limit=800, epsabs=0.0, epsrel=1e-11)[0]
         return tot
 
-    return integrate.quad(inner, 0.0, 1.0, limit=200, epsabs=0.0, epsrel=1e-9)[0]
+    return integrate.quad(inner, 0.0, 1.0, limit=400, epsabs=0.0, epsrel=1e-10)[0]
 
 
 def k_bar(sigma, kstar, eps=0.1):

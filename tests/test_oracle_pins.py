@@ -152,6 +152,26 @@ def test_cell_lookup_matches_definition(dec):
 
 
 # ---------------------------------------------------------------- synthesis / maps
+@pytest.mark.parametrize("sigma", [0.1, 0.5, 1.0])
+def test_lognormal_normalisation_and_width(sigma):
+    """Eq. eq_lognormal is a normalised Gaussian in ln k: its integral over ln k is the amplitude A, its mean
+    is ln k* and its variance sigma^2 (quadrature, not the closed form).  The dimensionful spectrum then gives
+    the same total variance, <zeta^2> = int d^3k/(2 pi)^3 P(k) = int P k^2 dk / (2 pi^2) = A, which pins the
+    2 pi^2 / k^3 of Eq. eq_adimensional_P as well."""
+    A, kstar = 3e-3, 7.5
+    lo, hi = np.log(kstar) - 12 * sigma, np.log(kstar) + 12 * sigma
+    f = lambda lk: synth.delta2_lognormal(np.exp(lk), A, sigma, kstar)
+    m0 = integrate.quad(f, lo, hi, epsabs=0, epsrel=1e-13, limit=200)[0]
+    m1 = integrate.quad(lambda lk: (lk - np.log(kstar)) * f(lk), lo, hi, epsabs=1e-14 * A, epsrel=1e-10, limit=200)[0]
+    m2 = integrate.quad(lambda lk: (lk - np.log(kstar)) ** 2 * f(lk), lo, hi, epsabs=0, epsrel=1e-12, limit=200)[0]
+    assert m0 == pytest.approx(A, rel=1e-10)
+    assert abs(m1) < 1e-12 * A
+    assert m2 / m0 == pytest.approx(sigma ** 2, rel=1e-10)
+    var = integrate.quad(lambda lk: synth.p_zeta(np.exp(lk), A, sigma, kstar) * np.exp(3 * lk) / (2 * np.pi ** 2),
+                         lo, hi, epsabs=0, epsrel=1e-13, limit=200)[0]
+    assert var == pytest.approx(A, rel=1e-10)
+
+
 def test_synthesis_hermitian_zeroed_and_normalised():
     """zeta_g is real (Hermitian spectrum), DC and Nyquist planes are zero, and the shell-averaged
     |zeta_g~|^2 / (V P_zeta) is 1 within sampling error (<X~X~*> = V P, Sec. sec_envelope_obs)."""
@@ -336,6 +356,50 @@ def test_seed_mean_matches_wick_expectation(dec):
                      for s in range(100, 164)])
     mean, se = vals.mean(0), vals.std(0, ddof=1) / np.sqrt(len(vals))
     assert np.all(np.abs(mean - ex["omega"]) < 4 * se), (mean, ex["omega"], se)
+
+
+def _semi_analytic_dense(k, A, sigma, kstar, n=3000):
+    """Eq. eq_semi_anal by a plain midpoint sum in other variables: x = ln(k(s+q)/2k*), y = ln(k(s-q)/2k*), in
+    which the two Delta^2 factors are Gaussians and dq ds = (s^2 - q^2)/2 dx dy; the domain q in [0, 1], s >= 1
+    is a mask on the grid (half weight on the q = 0 diagonal).  The kernel T of Eq. eq_semi_anal is written out
+    vectorised here; this pins the quadrature, not T (T is tied to the kernels I_s, I_c by the Wick-sum test)."""
+    lim = 9.0 * sigma
+    h = 2.0 * lim / n
+    x = -lim + h * (np.arange(n) + 0.5)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    c = 2.0 * kstar / k
+    up, um = c * np.exp(X), c * np.exp(Y)
+    s, q = (up + um) / 2.0, (up - um) / 2.0
+    ok = (q >= 0.0) & (q <= 1.0) & (s >= 1.0)
+    g = A / np.sqrt(2.0 * np.pi * sigma ** 2)
+    w = (g * np.exp(-X ** 2 / (2 * sigma ** 2)) * g * np.exp(-Y ** 2 / (2 * sigma ** 2)))[ok]
+    w *= np.where(np.eye(n, dtype=bool), 0.5, 1.0)[ok]
+    qq, ss = q[ok], s[ok]
+    lg = np.log(np.abs((3.0 - qq ** 2) / (3.0 - ss ** 2)))
+    T = 12.0 * (qq ** 2 + ss ** 2 - 6) ** 4 * (qq ** 2 - 1) ** 2 * (ss ** 2 - 1) ** 2 / (ss ** 2 - qq ** 2) ** 8 * (
+        (lg + 2.0 * (ss ** 2 - qq ** 2) / (qq ** 2 + ss ** 2 - 6)) ** 2 + np.pi ** 2 * (ss > np.sqrt(3.0)))
+    return float(np.sum(w * T * (ss ** 2 - qq ** 2) / 2.0) * h * h)
+
+
+@pytest.mark.parametrize("sigma", [0.5, 1.0])
+@pytest.mark.parametrize("k", [0.5, 1.0, 2.0])
+def test_semi_analytic_quadrature_converges(sigma, k):
+    """The adaptive quadrature of Eq. eq_semi_anal equals a plain midpoint sum of the same integral in other
+    variables (the two momenta's logarithms) to within that sum's own discretisation error (< 1 %).  A broad
+    peak (sigma = 1) is where a quadrature over a linear s axis loses the narrow peak of its integrand."""
+    a = semi_analytic.omega_gauss(k, 1e-2, sigma, 1.0)
+    b = _semi_analytic_dense(k, 1e-2, sigma, 1.0)
+    assert abs(a / b - 1) < 1e-2
+
+
+@pytest.mark.parametrize("k", [0.5, 1.5])
+def test_semi_analytic_narrow_peak_limit(k):
+    """As sigma -> 0, Delta^2 -> A delta(ln k/k*) and Eq. eq_semi_anal collapses onto q = 0, s0 = 2 k*/k: with
+    dq ds = (s^2 - q^2)/2 dx dy and half of the peak's mass on the q >= 0 side, Omega -> A^2 s0^2 T(0, s0) / 4.
+    (k = 0.5 and 1.5 keep s0 away from sqrt3 and sqrt6, where T varies too fast for the limit at sigma = 0.002.)"""
+    s0 = 2.0 / k
+    limit = 1e-4 * s0 ** 2 * semi_analytic.T_kernel(0.0, s0) / 4.0
+    assert semi_analytic.omega_gauss(k, 1e-2, 0.002, 1.0) == pytest.approx(limit, rel=5e-4)
 
 
 @pytest.mark.slow
