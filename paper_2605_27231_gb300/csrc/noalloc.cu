@@ -13,7 +13,9 @@
 //   g_tw_f32 / g_tw_f64: the FP64-generated twiddle tables of every supported N (8..128), 248 entries each.
 // Host code cannot use a __device__ array's name as a device address (in host code it names a host-side
 // stand-in), so the first call on each device looks the addresses up with cudaGetSymbolAddress while that
-// device is current, fills the twiddle tables, and caches the addresses for that device.
+// device is current, fills the twiddle tables, waits for the device, and caches the addresses for that device.
+// The cache lives as long as the process: resetting a device (cudaDeviceReset) after its first call here is
+// not supported, because the reloaded module would hold empty tables, possibly at other addresses.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -74,6 +76,10 @@ cudaError_t setup(int dev, DevState** out) {
       return e;
     if ((e = cudaMemcpy(s.tw64, t64.data(), sizeof(double2) * kTwEntries, cudaMemcpyHostToDevice)) != cudaSuccess)
       return e;
+    // A copy from pageable host memory may return before the data has reached the device, and the caller's
+    // stream may be a non-blocking one that is not ordered after these copies: wait for the device before
+    // any kernel can read the tables.
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     s.ready = true;
   }
   *out = &s;
