@@ -6,9 +6,13 @@
 // pool.  Every plan owns its CUDA stream, so the slots' batches overlap on the device.
 //
 // Admission by device memory: a new plan may be created only if its footprint fits the budget together with
-// the plans already resident; idle plans are evicted least-recently-used to make room.  When the oldest queued
-// request cannot be admitted, later requests may only reuse idle plans (no new allocation), so the head of the
-// queue cannot starve.  A request whose plan alone exceeds the budget is refused at submission (SIGW_EBUSY).
+// the plans already resident.  Only the oldest queued request may evict idle plans (least-recently-used first)
+// to make room, and only when the eviction frees enough.  A later request may create a plan only in budget that
+// is free without eviction and that the oldest request does not need (its footprint stays reserved while it has
+// no plan of its size class), otherwise it must reuse an idle plan.  While the oldest request cannot be admitted
+// even by evicting every idle plan, no later request starts, so finishing plans stay idle until the oldest
+// request can evict them: the head of the queue cannot starve, whichever slot (general or express) looks first.  A request whose plan alone exceeds the budget is refused at
+// submission (SIGW_EBUSY).
 // Plans run on streams whose priority falls with the lattice size (smaller lattices first), so short requests
 // are not held behind the thread blocks of long ones when they share the device.
 // Express slots (sigw_server_set_express) are extra workers that take only requests of small lattices (N at most
@@ -94,6 +98,13 @@ PoolPlan* idle_plan(sigw_server_s* s, int N, double L) {
   return nullptr;
 }
 
+// Whether any plan (idle, busy or being created) of size class (N, L) is in the pool.
+bool any_plan(sigw_server_s* s, int N, double L) {
+  for (PoolPlan* p : s->pool)
+    if (p->N == N && p->L == L) return true;
+  return false;
+}
+
 struct Doomed {
   sigw_plan plan;
   cudaStream_t stream;
@@ -121,8 +132,12 @@ int priority_for(int N) {
 }
 
 // Evict idle plans (least recently used first) until `need` more bytes fit.  Called with the lock held;
-// returns false if it cannot make room.
+// returns false, evicting nothing, if even evicting every idle plan would not make room.
 bool make_room(sigw_server_s* s, size_t need, std::vector<Doomed>* to_destroy) {
+  size_t idle = 0;
+  for (PoolPlan* p : s->pool)
+    if (!p->busy && !p->creating) idle += p->bytes;
+  if (s->in_use - idle + need > s->budget) return false;
   while (s->in_use + need > s->budget) {
     PoolPlan* lru = nullptr;
     for (PoolPlan* p : s->pool)
@@ -162,23 +177,38 @@ void worker_main(sigw_server_s* s, int max_N) {
     bool create = false;
     size_t need = 0;
     std::vector<Doomed> destroy;
-    bool first = true;
+    // Budget the oldest queued request keeps reserved: its footprint while no plan of its size class exists.
+    // If even evicting every idle plan would not make room for it, it is blocked: no later request may start
+    // (idle plans then stay idle until enough of them can be evicted for the oldest one).
+    size_t reserve = 0;
+    bool blocked = false;
+    if (!s->queue.empty() && !any_plan(s, s->queue.front()->N, s->queue.front()->L)) {
+      reserve = footprint_of(s, s->queue.front()->N);
+      size_t idle = 0;
+      for (PoolPlan* p : s->pool)
+        if (!p->busy && !p->creating) idle += p->bytes;
+      blocked = s->in_use - idle + reserve > s->budget;
+    }
     for (size_t qi = 0; qi < s->queue.size(); ++qi) {
       Req* r = s->queue[qi];
+      if (qi > 0 && blocked) break;
       if (max_N > 0 && r->N > max_N) continue;
       if ((use = idle_plan(s, r->N, r->L))) {
         head = r;
         break;
       }
-      if (first) {  // only the oldest request this slot may take may allocate
-        need = footprint_of(s, r->N);
+      need = footprint_of(s, r->N);
+      if (qi == 0) {  // the oldest request may evict idle plans
         if (make_room(s, need, &destroy)) {
           head = r;
           create = true;
           break;
         }
+      } else if (s->in_use + need + reserve <= s->budget) {  // the rest only in free, unreserved budget
+        head = r;
+        create = true;
+        break;
       }
-      first = false;
     }
     if (!head) {
       if (!destroy.empty()) {
@@ -344,14 +374,20 @@ sigw_status sigw_poll(sigw_server s, uint64_t ticket, double* omega, double* lat
 sigw_status sigw_wait(sigw_server s, uint64_t ticket, double timeout_s, double* omega, double* latency_s) {
   if (!s) return SIGW_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);
-  auto it = s->reqs.find(ticket);
-  if (it == s->reqs.end()) return SIGW_EINVAL;
-  Req* r = it->second;
   const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
-  while (r->state != 2) {
-    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout && r->state != 2) return SIGW_ETIMEOUT;
+  while (true) {
+    // Look the ticket up again after every wake: another thread may have taken (and freed) the result.
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return SIGW_EINVAL;
+    Req* r = it->second;
+    if (r->state == 2) return take_result(s, r, omega, latency_s);
+    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+      auto again = s->reqs.find(ticket);
+      if (again == s->reqs.end()) return SIGW_EINVAL;
+      if (again->second->state == 2) return take_result(s, again->second, omega, latency_s);
+      return SIGW_ETIMEOUT;
+    }
   }
-  return take_result(s, r, omega, latency_s);
 }
 
 sigw_status sigw_server_stats_read(sigw_server s, sigw_server_stats* out) {
