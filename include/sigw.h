@@ -196,8 +196,10 @@ const char* sigw_strerror(sigw_status s);
  * (continuous batching): max_slots worker threads each take the oldest admissible request together with
  * queued requests of the same size class (N, L), up to opts->max_batch, and run them as one batch on a plan of
  * a shared pool; plans own their streams, so slots overlap on the device.  A plan is created only if its
- * footprint (sigw_plan_footprint) fits hbm_budget_bytes beside the resident plans; idle plans are evicted
- * least-recently-used to make room, and only the oldest queued request may allocate (no starvation).
+ * footprint (sigw_plan_footprint) fits hbm_budget_bytes beside the resident plans.  Only the oldest queued
+ * request may evict idle plans (least-recently-used first, and only if that frees enough); later requests may
+ * allocate only budget that is free and not needed by the oldest one, and start nothing while the oldest one
+ * cannot be admitted even by eviction (no starvation).
  * All server calls are thread-safe.  No counterpart in the paper (which reports single timings,
  * Sec. sec_conclusions); this is the serving layer around its method. */
 typedef struct sigw_server_stats {
@@ -219,7 +221,8 @@ sigw_status sigw_submit(sigw_server srv, int N, double L, const sigw_pzeta* pz, 
  * ticket.  SIGW_EINVAL for an unknown ticket. */
 sigw_status sigw_poll(sigw_server srv, uint64_t ticket, double* omega, double* latency_s);
 
-/* As sigw_poll, but waits up to timeout_s seconds; SIGW_ETIMEOUT if the request is still not done. */
+/* As sigw_poll, but waits up to timeout_s seconds; SIGW_ETIMEOUT if the request is still not done.  If another
+ * thread takes the result first (sigw_poll or sigw_wait on the same ticket), this call returns SIGW_EINVAL. */
 sigw_status sigw_wait(sigw_server srv, uint64_t ticket, double timeout_s, double* omega, double* latency_s);
 
 sigw_status sigw_server_stats_read(sigw_server srv, sigw_server_stats* out);
@@ -295,14 +298,23 @@ sigw_status sigw_cell_table(const sigw_opts* opts, int n_c, int msq_max, int16_t
  * values, plus 248-entry twiddle tables per precision), held by every GPU that loads the library until the
  * process exits.  Limit: N*N*(N/2) complex values must fit in 8 MiB, i.e. N <= 128 in FP32 and N <= 64 in
  * FP64 (N a power of two >= 8); larger N returns SIGW_EINVAL.  The first call on a device sets that device up
- * (looks up the arrays' device addresses and fills the twiddles, synchronously); make that first call before
- * any stream capture.  Work is queued on cuda_stream (NULL: the legacy default stream); the call does not
+ * (looks up the arrays' device addresses, fills the twiddles and waits for the whole device, so that a
+ * non-blocking stream sees the tables); make that first call before any stream capture.  The set-up is cached
+ * for the life of the process: resetting the device (cudaDeviceReset) after its first call is not supported.  Work is queued on cuda_stream (NULL: the legacy default stream); the call does not
  * wait.  All calls share the one scratch array, which keeps the last call's contents (every call overwrites
  * all of what it reads, so nothing needs clearing): calls that overlap on the GPU (different streams, or a
  * second call before the first finished on another stream) race and give wrong results.
  * Errors: SIGW_EINVAL (arguments or size limit), SIGW_ECUDA (set-up or launch failed). */
 sigw_status sigw_fft3d_noalloc(int N, int precision, int direction, const void* in_dev, void* out_dev,
                                void* cuda_stream);
+
+/* Test hook for failure handling (no counterpart in the paper): the bounded waits in the main loop of the last
+ * inverse pass (the bulk-copy ring) give up after `cycles` clock cycles instead of about a second (cycles = 0
+ * restores the default).  A tiny limit makes waits give up while every copy still completes normally: the
+ * spectrum call then returns SIGW_ETIMEOUT (results invalid), every copy in flight has landed before its CTA
+ * exits, and the plan stays usable.  Applies to launches queued after the call (a captured all-shells graph is
+ * dropped and captured again).  Errors: SIGW_EINVAL (NULL plan, cycles < 0). */
+sigw_status sigw_plan_debug_wait_limit(sigw_plan plan, long long cycles);
 
 /* Test hook for failure handling: the next `n`-th device allocation made by the library fails with
  * SIGW_ENOMEM (n = 1: the next one; n <= 0 disables).  Affects the calling process only. */

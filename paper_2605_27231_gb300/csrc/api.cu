@@ -139,6 +139,7 @@ struct sigw_plan_s {
   unsigned long long* d_hits = nullptr;
   uint64_t* d_seeds = nullptr;
   int* d_err = nullptr;  // OR-ed by kernels whose bounded waits gave up
+  long long wait_limit = sigw::kDefaultWaitLimit;  // cycles of P3's main-loop waits (sigw_plan_debug_wait_limit)
   int* d_shells_all = nullptr;   // 1..N/2, for the all-shells call (no upload, so it can be captured)
   double* d_Nk_all = nullptr;
   // CUDA graph of the all-shells spectrum loop, per realisation count
@@ -738,7 +739,8 @@ static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, con
             OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, var, st));
       }
       RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
-          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, var, st));
+          OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, p->wait_limit,
+              var, st));
       RUN(p, 4, 6.0 * batch * ((double)NN * ncp + (double)N * nk1 * ncp) * cel, "F2",
           OPS(p, f2, N, p->d_F, p->d_F2, n_c, batch, p->d_tw, st));
       if (!jk) {
@@ -1086,7 +1088,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, st);
         cudaError_t e = OPS(p, p3, N, p->d_work, p->d_sigma[0], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err,
-                            v3 ? 2 : 0, st);
+                            sigw::kDefaultWaitLimit, v3 ? 2 : 0, st);
         cudaEventRecord(e1, st);
         if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&t3[v3], e0, e1) != cudaSuccess) {
@@ -1185,6 +1187,16 @@ sigw_status sigw_plan_set_tuning(sigw_plan p, int alpha_batch, int variant) {
   p->B = alpha_batch;
   p->variant = variant;
   if (p->graph) {  // the captured loop used the old choice
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  return SIGW_OK;
+}
+
+sigw_status sigw_plan_debug_wait_limit(sigw_plan p, long long cycles) {
+  if (!p || cycles < 0) return SIGW_EINVAL;
+  p->wait_limit = cycles > 0 ? cycles : sigw::kDefaultWaitLimit;
+  if (p->graph) {  // a captured graph holds the old limit in its kernel arguments
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
   }

@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(TC_ * (N / E_), ((E_ >= 32 || TC_ * (N / E_) >
 }
 
 // ---------------------------------------------------------------- bulk-copy pipeline helpers
-// cp.async.bulk (TMA, 1-D) global -> shared with mbarrier completion.  Waits are bounded: after about a
-// second of spinning the wait sets *err and gives up, so a lost copy can never hang the GPU.
+// cp.async.bulk (TMA, 1-D) global -> shared with mbarrier completion.  Waits are bounded: after `limit` clock
+// cycles (about a second by default) the wait sets *err and gives up, so a lost copy can never hang the GPU.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -511,18 +511,30 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// With the default limit the wait uses try_wait, which may suspend the thread for a while inside the instruction;
+// with a shorter limit (a test's) it polls with the non-blocking test_wait, so the limit is what decides.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          long long limit = kDefaultWaitLimit) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
+  const bool poll = limit < kDefaultWaitLimit;
   while (true) {
     uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
+    if (poll) {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(done)
+          : "r"(a), "r"(parity)
+          : "memory");
+    } else {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(done)
+          : "r"(a), "r"(parity)
+          : "memory");
+    }
     if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, 1);
       return false;
     }
@@ -652,13 +664,17 @@ __device__ __forceinline__ void accum6<float, true>(float sa, float g0, float2 z
 // then the forward R2C of s_ij along axis 2 keeping k2 = 0..n_c, written to F[b][comp][a0][a1][k2].
 // Term pair (a, a+1) uses three complex transforms: (g2^a + i g1^a), (g0^a + i g0^{a+1}), (g2^{a+1} + i g1^{a+1}).
 // The six packed rows of a term pair stream into a STAGES-deep shared-memory ring by cp.async.bulk,
-// issued STAGES-1 pairs ahead by thread 0.
+// issued STAGES-1 pairs ahead by thread 0.  Bounded waits: the main loop's waits give up after wait_limit cycles
+// (normally kDefaultWaitLimit; a test passes a tiny limit, so that waits give up while the copies still land).
+// A thread whose wait gave up sets *err, stops waiting and (thread 0) stops issuing copies; before the CTA exits,
+// thread 0 waits, with the default limit, for the last copy issued into each stage, so no bulk copy can still be
+// writing into the CTA's shared memory after it has exited.  The results of a launch that set *err are invalid.
 template <typename T, int N, int E_ = ((N >= 16) ? 8 : 4)>
 __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>* __restrict__ W,
                                                                    const T* __restrict__ sigma, int n_alpha,
                                                                    cx<T>* __restrict__ F, int n_c,
                                                                    const cx<T>* __restrict__ tw,
-                                                                   int* __restrict__ err) {
+                                                                   int* __restrict__ err, long long wait_limit) {
   using CF = P3Cfg<T, N, E_>;
   constexpr int E = CF::E, P = CF::P, H = N / 2, RPC = CF::RPC, STAGES = CF::STAGES;
   using Sync = typename RowSync<P>::type;
@@ -703,10 +719,14 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
   }
   const T fj = (T)j;
   bool ok = true;
+  int issued = STAGES - 1 < npairs ? STAGES - 1 : npairs;  // term pairs whose copies thread 0 has issued
   for (int pr = 0; pr < npairs; ++pr) {
     const int s = pr % STAGES;
-    if (threadIdx.x == 0 && pr + STAGES - 1 < npairs) issue(pr + STAGES - 1);
-    if (ok) ok = mbar_wait(bars + s, (uint32_t)((pr / STAGES) & 1), err);
+    if (threadIdx.x == 0 && ok && pr + STAGES - 1 < npairs) {
+      issue(pr + STAGES - 1);
+      issued = pr + STAGES;
+    }
+    if (ok) ok = mbar_wait(bars + s, (uint32_t)((pr / STAGES) & 1), err, wait_limit);
     const int a = 2 * pr;
     const bool two = a + 1 < n_alpha;
     const cx<T>* st = ring + s * CF::STAGE_ELEMS + rr * H;
@@ -746,6 +766,14 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
       for (int r = 0; r < E; ++r) accum6<T, (sizeof(T) == 4 && N <= 256)>(sb, zB[r].y, z[r], a0[r], a21[r], a43[r], a5[r]);
     }
     __syncthreads();  // stage s fully read before it is refilled
+  }
+  if (threadIdx.x == 0) {
+    // The last copy issued into each stage has landed before the CTA may exit (immediate when every wait
+    // succeeded; after a wait gave up, the copies still in flight are waited for with the default limit).
+    for (int s = 0; s < STAGES && s < issued; ++s) {
+      const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
+      mbar_wait(bars + s, (uint32_t)((last / STAGES) & 1), err);
+    }
   }
   // forward R2C of the six real rows (00, 11 | 22, 01 | 02, 12), two per complex transform
   cx<T>* zb = L.buf(0);

@@ -8,6 +8,8 @@
 namespace sigw {
 
 // Tile shapes chosen per (precision, N); exposed so the host can size buffers.
+constexpr long long kDefaultWaitLimit = 1ll << 31;  // clock cycles of a bounded wait, about one second
+
 struct LaunchShape {
   int tc_strided;   // columns per CTA in strided passes
   int tc_f3;        // columns per CTA in the forward-axis-0 / TT / bin pass
@@ -52,11 +54,12 @@ struct OpsRT {
   static cudaError_t p2(int N, const void* Ta, const void* Tb, void* W, int n_alpha, int alpha0, int nb, int batch,
                         const void* tw, int variant, cudaStream_t st);
   // last inverse pass (axis 2, C2R) + sum_a sigma_a g_i g_j + forward R2C along axis 2 keeping k2 <= n_c
-  // err: device int, OR-ed with 1 when a bounded wait of the bulk-copy pipeline gives up.
+  // err: device int, OR-ed with 1 when a bounded wait of the bulk-copy pipeline gives up; wait_limit: clock
+  // cycles after which a wait of the main loop gives up (kDefaultWaitLimit unless a test shrinks it).
   // variant bit 2 selects the radix-16 form where p3_variants(N) == 2.
   static int p3_variants(int N);
   static cudaError_t p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
-                        const void* tw, int* err, int variant, cudaStream_t st);
+                        const void* tw, int* err, long long wait_limit, int variant, cudaStream_t st);
   // forward pass along axis 1 keeping |n1| <= n_c
   static cudaError_t f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st);
   // forward pass along axis 0 + TT projection + shell sum -> per-CTA FP64 partials; with Xj (nullable) also the

@@ -111,21 +111,22 @@ struct OpsT {
   }
   template <int N, int E>
   static cudaError_t p3_v(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
-                          int* err, cudaStream_t st) {
+                          int* err, long long wait_limit, cudaStream_t st) {
     using CF = P3Cfg<T, N, E>;
     auto k = k_p3<T, N, E>;
     SIGW_CHECK_LAUNCH(allow_smem(k, CF::SMEM));
     dim3 grid((N * N) / CF::RPC, batch);
-    k<<<grid, CF::THREADS, CF::SMEM, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw, err);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw, err,
+                                           wait_limit);
     return cudaGetLastError();
   }
   template <int N>
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
-                          int* err, int variant, cudaStream_t st) {
+                          int* err, long long wait_limit, int variant, cudaStream_t st) {
     if constexpr (AltP3<T, N>::exists) {
-      if (variant & 2) return p3_v<N, AltP3<T, N>::E>(W, sigma, n_alpha, F, n_c, batch, tw, err, st);
+      if (variant & 2) return p3_v<N, AltP3<T, N>::E>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
     }
-    return p3_v<N, ((N >= 16) ? 8 : 4)>(W, sigma, n_alpha, F, n_c, batch, tw, err, st);
+    return p3_v<N, ((N >= 16) ? 8 : 4)>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
   }
   static void n1_range(int N, int n_c, int* lo, int* nk1) {
     const int H = N / 2;
@@ -296,8 +297,9 @@ cudaError_t OpsRT<T>::p2(int N, const void* Ta, const void* Tb, void* W, int n_a
 }
 template <typename T>
 cudaError_t OpsRT<T>::p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
-                      const void* tw, int* err, int variant, cudaStream_t st) {
-  SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, err, variant, st)));
+                      const void* tw, int* err, long long wait_limit, int variant, cudaStream_t st) {
+  SIGW_DISPATCH_N(N, return (OpsT<T>::template p3_n<NN>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit,
+                                                       variant, st)));
 }
 template <typename T>
 cudaError_t OpsRT<T>::f2(int N, const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st) {

@@ -93,6 +93,7 @@ def lib():
         "sigw_decompose": (C.c_int, [C.POINTER(Opts), C.c_int, _dbl, _dbl, _dbl, _dbl]),
         "sigw_cell_table": (C.c_int, [C.POINTER(Opts), C.c_int, C.c_int, C.POINTER(C.c_int16)]),
         "sigw_debug_fail_alloc": (C.c_int, [C.c_int]),
+        "sigw_plan_debug_wait_limit": (C.c_int, [P, C.c_longlong]),
         "sigw_plan_profile": (C.c_int, [P, C.c_int]),
         "sigw_plan_autotune": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dbl]),
         "sigw_fft3d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P]),
@@ -323,6 +324,10 @@ class Plan:
         sh = np.arange(1, self.N // 2 + 1, dtype=np.int32) if shells is None else np.ascontiguousarray(shells, dtype=np.int32)
         _check(lib().sigw_spectrum_async(self._h, _ptr(sh, C.c_int), len(sh), C.c_void_p(dev_out_ptr)), self._h,
                "sigw_spectrum_async")
+
+    def debug_wait_limit(self, cycles):
+        """sigw_plan_debug_wait_limit: test hook; 0 restores the default limit of the bulk-copy waits."""
+        _check(lib().sigw_plan_debug_wait_limit(self._h, int(cycles)), self._h, "sigw_plan_debug_wait_limit")
 
     def copy_phi(self, b=0):
         out = np.zeros((self.N, self.N, self.N // 2 + 1), dtype=self.dtype)

@@ -102,6 +102,24 @@ def test_omega_all_shells_small(lib, dec, N, kind, F, precision):
 
 
 @pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("F,G", [(0.0, 1.0), (0.0, 50.0), (3.0, 10.0)])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_cubic_gnl_all_shells(lib, dec, N, F, G, precision):
+    """The cubic term of the local map (Sec. "Local Non-Gaussianities": F_NL = 0 with G_NL in {1, 5, 10, 50}, and a
+    mixed F_NL, G_NL case): Phi~ element by element and every shell against the oracle."""
+    spec = workloads.Spec(N=N, L=1.0, A=1e-2, sigma=0.5, kstar=(N // 4) * 2 * np.pi, kind="local", F_NL=F, G_NL=G,
+                          seed=19)
+    ref, Phi, _ = _oracle(spec, dec, None)
+    got, phi, _ = _gpu(lib, spec, None, precision)
+    refh = Phi[:, :, :N // 2 + 1]
+    assert np.abs(phi - refh).max() <= (1e-12 if precision == 64 else 3e-6) * np.abs(refh).max()
+    np.testing.assert_array_equal(got["Nk"][0], ref["Nk"])
+    np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=RTOL[precision])
+    np.testing.assert_allclose(got["PA"][0], ref["PA"], rtol=RTOL[precision])
+    np.testing.assert_allclose(got["PB"][0], ref["PB"], rtol=RTOL[precision])
+
+
+@pytest.mark.parametrize("N", [16, 32])
 @pytest.mark.parametrize("precision", [64, 32])
 def test_nonlocal_map_all_shells(lib, dec, N, precision):
     """Eq. eq_nonlocal (alpha_NL = 5, beta_NL = -3 in units of 1/k*^2): Phi~ and every shell against the oracle."""
@@ -217,6 +235,27 @@ def test_injected_allocation_failure_reports_enomem(lib):
         assert np.all(np.isfinite(p.spectrum()["omega"]))
 
 
+@pytest.mark.parametrize("N", [64, 128])
+def test_bulk_copy_wait_timeout_is_reported_and_recoverable(lib, dec, N):
+    """The last inverse pass's bounded waits (bulk-copy ring) given a one-cycle limit give up while every copy
+    still lands: the call reports SIGW_ETIMEOUT; with the default limit restored the same plan gives the oracle's
+    values, on direct launches and on the (re-captured) all-shells graph."""
+    spec = workloads.Spec(N=N, L=1.0, A=1e-2, sigma=0.5, kstar=(N // 8) * 2 * np.pi, kind="local", F_NL=2.0, seed=23)
+    shells = [3, N // 4]
+    ref, _, _ = _oracle(spec, dec, shells)
+    with lib.Plan(N, spec.L, precision=32) as p:
+        p.generate_spec(spec)
+        first = p.spectrum()["omega"][0]  # captures the all-shells graph with the default limit
+        for call in (lambda: p.spectrum(shells), lambda: p.spectrum()):
+            p.debug_wait_limit(1)
+            with pytest.raises(lib.SigwError) as e:
+                call()
+            assert e.value.status == lib.ETIMEOUT
+            p.debug_wait_limit(0)
+            np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
+            assert np.array_equal(p.spectrum()["omega"][0], first)
+
+
 def test_usr_strict_mode(lib):
     spec = workloads.Spec(N=16, L=1.0, A=5e-1, sigma=0.5, kstar=4 * 2 * np.pi, kind="usr", seed=2)
     with lib.Plan(16, 1.0, n_alpha=2, strict_domain=1, precision=64) as p:
@@ -247,6 +286,54 @@ def test_usr256_sampled_shell_fp32(lib, dec):
     got, _, ghits = _gpu(lib, spec, shells, 32)
     np.testing.assert_allclose(got["omega"][0], ref["omega"], rtol=1e-4)
     assert abs(int(ghits[0]) - hits) <= max(2, hits // 100)
+
+
+def _golden(name):
+    """Per-shell oracle values written by tests/golden/make_golden.py (oracle only): rows n_c N_k Omega P_A P_B,
+    and the USR floor-hit count of the realisation."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    hits = None
+    for line in open(path):
+        if line.startswith("# usr_floor_hits="):
+            hits = int(line.split("=")[1])
+    return np.loadtxt(path, comments="#", ndmin=2), hits
+
+
+def _worst(got, ref):
+    rel = np.abs(got / ref - 1.0)
+    i = int(np.argmax(rel))
+    return rel[i], i
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,seed,fname", [("local128", 2, "local128_seed2.txt"), ("usr256", 1, "usr256_seed1.txt"),
+                                             ("broad512", 5, "broad512_seed5.txt")])
+def test_full_size_fp32_every_stored_shell(lib, name, seed, fname):
+    """FP32 Omega, P_A, P_B within 1e-4 relative of the FP64 oracle in every stored shell bin at full size, N_k
+    exact.  usr256 runs in the bench's launch configuration (four seeds per launch, autotuned plan, the captured
+    all-shells graph); its first seed is compared.  local128 compares all 64 shells, broad512 shells 8 and 32."""
+    rows, hits = _golden(fname)
+    spec = workloads.workload(name, seed=seed)
+    shells = rows[:, 0].astype(int)
+    full = len(shells) == spec.N // 2
+    if name == "usr256":
+        with lib.Plan(spec.N, spec.L, precision=32, max_batch=4) as p:
+            ghits = p.generate_spec(spec, seeds=list(workloads.USR256_SEEDS))
+            p.autotune()
+            out = p.spectrum()
+        got = {k: out[k][0] for k in ("omega", "PA", "PB", "Nk")}
+        assert abs(int(ghits[0]) - hits) <= max(2, hits // 100)
+    else:
+        with lib.Plan(spec.N, spec.L, precision=32) as p:
+            p.generate_spec(spec)
+            out = p.spectrum(None if full else shells)
+        got = {k: out[k][0] for k in ("omega", "PA", "PB", "Nk")}
+    np.testing.assert_array_equal(got["Nk"], rows[:, 1].astype(np.int64))
+    for col, key in ((2, "omega"), (3, "PA"), (4, "PB")):
+        w, i = _worst(got[key], rows[:, col])
+        print("%s %s: worst relative error %.3g at shell %d" % (name, key, w, shells[i]))
+        assert w <= 1e-4, (key, w, int(shells[i]))
 
 
 @pytest.mark.slow
