@@ -10,8 +10,16 @@ N/2 shells for one seed.
           (parameters in, results left in HBM); device time from CUDA events on the
           library's stream, max over ranks.
   e2e   : the same through sigw_generate + sigw_spectrum (host seeds in, host Omega out),
-          host copies inside the timed region.
+          host copies inside the timed region (a bounded number of steps, stated).
 Every rank processes its own seeds (no collective on the data path): "scaling": "weak".
+
+Rank 0 also reports (extra keys of the same line):
+  path_fraction : the step against the method's algorithmic bytes (312 field-FFTs per shell, each read + written once)
+  fp64_path     : one full FP64 spectrum of the same workload, timed (the metric's second number)
+  broad512      : one FP32 512^3 spectrum (per-kernel GB/s, clocks) and the FP64 path on sampled shells
+  serving       : the continuous-batching server at 0.5 / 0.8 / 1.0 of its measured capacity on the mixed request
+                  stream (FP32), and FP32 against the FP64 plain path on the small-lattice mix
+  cpu_baseline, paper_workload_scan, fft_crosscheck_cufft
 
 --impl reference times the CPU FP64 oracle on a bounded sample of the same workload
 (one target shell, a few separable terms) and extrapolates to spectra/s.
@@ -31,6 +39,7 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+METRIC = "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path; serving p50/p99 under serving)"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu capture per kernel kind at 256^3 FP32,
 # with the algorithmic bytes of the captured launch (the committed ncu summaries of k_p1, k_p2, k_p3 at 256^3).  These kernels move bytes in
@@ -169,11 +178,12 @@ def run_ours(args):
     ms_max = float(t.item())
     value = ws * batch * args.steps / (ms_max / 1e3)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (a bounded number of steps of the same work)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     barrier()
     plan.profile(False)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         plan.generate_spec(spec, seeds=seeds)
         res = plan.spectrum()
     barrier()
@@ -182,7 +192,7 @@ def run_ours(args):
     t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * batch * args.steps / float(t.item())
+    e2e_value = ws * batch * e2e_steps / float(t.item())
     omega_ok = bool(np.all(np.isfinite(res["omega"])) and np.all(res["omega"] > 0))
 
     # ---- dominant kernel roofline
@@ -201,51 +211,34 @@ def run_ours(args):
     launches = sum(prof[k]["launches"] for k in sigw.KINDS)
     plan.close()
 
-    # ---- FP64 path on the same GPU (sampled shells, extrapolated to a spectrum)
+    # ---- FP64 path on the same GPU: one full spectrum (all shells) of the same workload, timed
     fp64 = None
-    if rank == 0 and args.fp64_shells > 0:
-        with sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=64, max_batch=1) as p64:
-            shells = np.unique(np.linspace(1, n_sh, args.fp64_shells).astype(np.int32))
-            p64.generate_spec(spec, seeds=seeds[:1])
-            p64.spectrum(shells[:1])
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            p64.generate_spec(spec, seeds=seeds[:1])
-            b.record(stream)
-            b.synchronize()
-            gen_ms = a.elapsed_time(b)
-            a.record(stream)
-            p64.spectrum_async(dev_out.data_ptr(), shells)
-            b.record(stream)
-            b.synchronize()
-            sh_ms = a.elapsed_time(b)
-        per_spec_s = (gen_ms + sh_ms * n_sh / len(shells)) / 1e3
-        fp64 = {"value": 1.0 / per_spec_s, "unit": "spectra/s", "dtype": "f64",
-                "sample": "1 seed, shells %s of 1..%d, extrapolated to all shells" % (shells.tolist(), n_sh),
-                "fp32_over_fp64": (value / ws) / (1.0 / per_spec_s)}
+    if rank == 0 and args.fp64_spectrum:
+        fp64 = fp64_spectrum(spec, seeds[0], stream, value / ws)
+    big = None
+    if rank == 0 and args.broad512:
+        big = broad512_leg(stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(spec, args.cpu_terms)
     serving = None
     if rank == 0 and args.serve_requests > 0:
-        serving = serving_run(args)
+        serving = serving_study(args)
     scan = paper_scan() if rank == 0 and not args.no_paper_scan else None
     fftx = fft_crosscheck() if rank == 0 and not args.no_paper_scan else None
 
     if rank == 0:
         line = {
-            "metric": "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path)",
-            "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == 32 else "f64",
             "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
             "config": dict(workload_config(args, spec),
                            l2="inputs larger than L2 (%.1f GB device working set per step)" % (sigw.footprint(
                                spec.N, sigw.default_opts(max_batch=batch)) / 1e9), autotuned=tuned),
-            "e2e": {"value": e2e_value, "unit": "spectra/s", "h2d_bytes_per_step": io["h2d_bytes"] / args.steps,
-                    "d2h_bytes_per_step": io["d2h_bytes"] / args.steps},
+            "e2e": {"value": e2e_value, "unit": "spectra/s", "h2d_bytes_per_step": io["h2d_bytes"] / e2e_steps,
+                    "d2h_bytes_per_step": io["d2h_bytes"] / e2e_steps, "steps": e2e_steps},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -254,7 +247,9 @@ def run_ours(args):
                          "peak_source": pk_src + " (copy)"},
             "kernels": kernels,
             "clocks": clocks,
+            "path_fraction": path_fraction(spec.N, value, peaks["hbm_gbs"]),
             "fp64_path": fp64,
+            "broad512": big,
             "cpu_baseline": cpu,
             "serving": serving,
             "paper_workload_scan": scan,
@@ -266,56 +261,178 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_run(args):
-    """Poisson replay of mixed spectrum requests through the continuous-batching server (sigw_submit).
-
-    Service times of one request per size class (alone, plans resident) give the single-slot capacity;
-    requests then arrive at args.serve_load times that rate.  Latency = completion - submission."""
+def _pct(v, q):
     import numpy as np
+    return float(np.percentile(v, q)) if len(v) else None
+
+
+def serving_leg(args, precision, sizes, loads, n_requests):
+    """Poisson replays of mixed spectrum requests through one continuous-batching server (sigw_submit).
+
+    The server's plans are made resident first.  Capacity = requests/s the server sustains on the mix: for each
+    size class a full batch (max_batch requests) is submitted at once and timed to completion, giving the
+    per-request cost c_N; capacity = 1 / mean_N c_N (N uniform over `sizes`).  Each load then replays
+    `n_requests` Poisson arrivals (seed 7) at load x capacity; latency = completion - submission."""
     from paper_2605_27231_gb300 import sigw
-    sizes = (64, 128, 256)
     srv = sigw.Server(args.serve_budget_gb * 1e9, max_slots=args.serve_slots, max_batch=args.serve_batch,
-                      precision=32)
+                      precision=precision)
     if args.serve_express > 0:
         srv.set_express(args.serve_express, args.serve_express_max_n)
+    out = {"precision": precision, "sizes": list(sizes), "slots": args.serve_slots, "max_batch": args.serve_batch,
+           "express_slots": args.serve_express, "express_max_n": args.serve_express_max_n,
+           "budget_gb": args.serve_budget_gb, "loads": []}
     try:
-        service = {}
-        for N in sizes:  # warm plans, then time one request alone
-            spec = workloads.serving_stream(1, 1.0, seed=1, sizes=(N,))[0][1]
-            srv.wait(srv.submit(spec))
+        cost = {}
+        for N in sizes:
+            specs = [sp for _, sp in workloads.serving_stream(args.serve_batch, 1.0, seed=1, sizes=(N,))]
+            for _ in range(2):  # plan made resident, graphs captured for the batch sizes the slots form
+                for t in [srv.submit(sp) for sp in specs]:
+                    srv.wait(t, timeout_s=3600)
             t0 = time.perf_counter()
-            srv.wait(srv.submit(spec))
-            service[N] = time.perf_counter() - t0
-        mean_service = sum(service.values()) / len(service)
-        rate = args.serve_load / mean_service
-        stream = workloads.serving_stream(args.serve_requests, rate, seed=7, sizes=sizes)
-        t_start = time.perf_counter()
-        tickets = []
-        for t_arr, spec in stream:
-            d = t_start + t_arr - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            tickets.append((spec.N, srv.submit(spec)))
-        lat = {N: [] for N in sizes}
-        for N, t in tickets:
-            om, l = srv.wait(t, timeout_s=1200)
-            lat[N].append(l)
-        t_end = time.perf_counter()
-        st = srv.stats()
+            for t in [srv.submit(sp) for sp in specs]:
+                srv.wait(t, timeout_s=3600)
+            cost[N] = (time.perf_counter() - t0) / len(specs)
+        capacity = 1.0 / (sum(cost.values()) / len(cost))
+        out["per_request_cost_s"] = {str(N): c for N, c in cost.items()}
+        out["capacity_req_per_s"] = capacity
+        for load in loads:
+            stats0 = srv.stats()
+            rate = load * capacity
+            stream = workloads.serving_stream(n_requests, rate, seed=7, sizes=sizes)
+            t_start = time.perf_counter()
+            tickets = []
+            for t_arr, sp in stream:
+                d = t_start + t_arr - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append((sp.N, srv.submit(sp)))
+            lat = {N: [] for N in sizes}
+            for N, t in tickets:
+                _, l = srv.wait(t, timeout_s=3600)
+                lat[N].append(l)
+            t_end = time.perf_counter()
+            st = srv.stats()
+            allv = sorted(l for v in lat.values() for l in v)
+            out["loads"].append({
+                "load": load, "requests": len(allv), "arrival_rate_hz": rate, "spectra_per_s": len(allv) / (t_end - t_start),
+                "p50_latency_s": _pct(allv, 50), "p99_latency_s": _pct(allv, 99),
+                "per_size": {str(N): {"n": len(v), "p50_s": _pct(v, 50), "p99_s": _pct(v, 99)} for N, v in lat.items()},
+                "batches": st["batches"] - stats0["batches"],
+                "express_batches": st["express_batches"] - stats0["express_batches"],
+                "hbm_peak_gb": st["hbm_peak"] / 1e9})
     finally:
         srv.close()
-    allv = sorted(l for v in lat.values() for l in v)
-    pct = lambda v, q: float(np.percentile(v, q)) if v else None
-    return {"requests": len(allv), "arrival_rate_hz": rate, "load": args.serve_load,
-            "single_request_service_s": service, "spectra_per_s": len(allv) / (t_end - t_start),
-            "p50_latency_s": pct(allv, 50), "p99_latency_s": pct(allv, 99),
-            "per_size": {str(N): {"n": len(v), "p50_s": pct(v, 50), "p99_s": pct(v, 99)} for N, v in lat.items()},
-            "slots": args.serve_slots, "max_batch": args.serve_batch, "batches": st["batches"],
-            "express_slots": args.serve_express, "express_max_n": args.serve_express_max_n,
-            "express_batches": st["express_batches"],
-            "hbm_peak_gb": st["hbm_peak"] / 1e9, "budget_gb": args.serve_budget_gb,
-            "mix": "N uniform over {64,128,256}; f_NL ~ U[-5,20]; sigma ~ U[0.1,1]; map uniform over "
-                   "{gauss, local, usr}; Poisson arrivals, seed 7; FP32"}
+    return out
+
+
+def serving_study(args):
+    """FP32 serving of the full request mix (N in {64, 128, 256}) at 0.5, 0.8 and 1.0 of measured capacity, and
+    FP32 against the FP64 plain path on the small-lattice mix (N in {64, 128}; an FP64 256^3 request takes ~47 s,
+    so the full mix does not fit a benchmark run in FP64)."""
+    sizes = tuple(int(x) for x in args.serve_sizes.split(","))
+    loads = tuple(float(x) for x in args.serve_loads.split(","))
+    res = {"mix": "N uniform over the sizes; f_NL ~ U[-5,20]; sigma ~ U[0.1,1]; A = 1e-2; map uniform over "
+                  "{gauss, local, usr}; k* = N/8 k_f; seed = request id; Poisson arrivals, seed 7",
+           "fp32": serving_leg(args, 32, sizes, loads, args.serve_requests)}
+    if args.serve_fp64_requests > 0:
+        small = tuple(int(x) for x in args.serve_fp64_sizes.split(","))
+        res["fp32_small_mix"] = serving_leg(args, 32, small, (args.serve_fp64_load,), args.serve_requests)
+        res["fp64_small_mix"] = serving_leg(args, 64, small, (args.serve_fp64_load,), args.serve_fp64_requests)
+    main = [l for l in res["fp32"]["loads"] if abs(l["load"] - 0.8) < 1e-9] or res["fp32"]["loads"]
+    res["p50_latency_s"], res["p99_latency_s"] = main[0]["p50_latency_s"], main[0]["p99_latency_s"]
+    res["spectra_per_s"] = main[0]["spectra_per_s"]
+    res["headline_load"] = main[0]["load"]
+    return res
+
+
+def fp64_spectrum(spec, seed, stream, fp32_per_gpu):
+    """The FP64 plain path on the same GPU: one full spectrum (synthesis + all N/2 shells) of one realisation,
+    timed with CUDA events on the plan's stream, with the clocks sampled meanwhile."""
+    import torch
+    from paper_2605_27231_gb300 import sigw
+    dev_out = torch.empty(spec.N // 2 * 4, dtype=torch.float64, device="cuda")
+    with sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=64, max_batch=1) as p:
+        p.generate_spec(spec, seeds=[seed])
+        p.spectrum([1])  # warm
+        torch.cuda.synchronize()
+        clk = Clocks(torch.cuda.current_device())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p.generate_spec(spec, seeds=[seed])
+        p.spectrum_async(dev_out.data_ptr())
+        b.record(stream)
+        b.synchronize()
+        clocks = clk.stop()
+        s = a.elapsed_time(b) / 1e3
+    return {"value": 1.0 / s, "unit": "spectra/s", "dtype": "f64", "seconds_per_spectrum": s,
+            "sample": "1 seed, all %d shells, timed (not extrapolated)" % (spec.N // 2),
+            "fp32_over_fp64": fp32_per_gpu * s, "clocks": clocks}
+
+
+def broad512_leg(stream):
+    """The 512^3 broad-peak workload (local f_NL = -2, sigma = 1, k* = 64 k_f): one FP32 spectrum (all 256 shells,
+    one realisation) timed by CUDA events with per-kernel GB/s; the FP64 path on four sampled shells (labelled as
+    sampled: a full FP64 512^3 spectrum takes ~15 minutes)."""
+    import numpy as np
+    import torch
+    from paper_2605_27231_gb300 import sigw
+    spec = workloads.workload("broad512")
+    n_sh = spec.N // 2
+    dev_out = torch.empty(n_sh * 4, dtype=torch.float64, device="cuda")
+    peaks, _ = _peaks()
+    out = {"workload": "broad512", "N": spec.N, "map": spec.kind, "F_NL": spec.F_NL, "sigma": spec.sigma}
+    with sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=32, max_batch=1) as p:
+        p.generate_spec(spec)
+        p.spectrum([1])  # warm
+        torch.cuda.synchronize()
+        clk = Clocks(torch.cuda.current_device())
+        p.profile(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p.generate_spec(spec)
+        p.spectrum_async(dev_out.data_ptr())
+        b.record(stream)
+        b.synchronize()
+        prof = p.profile_read()
+        p.profile(False)
+        out["clocks"] = clk.stop()
+        s32 = a.elapsed_time(b) / 1e3
+        om = dev_out.view(n_sh, 4)[:, 3].cpu().numpy()
+    out["fp32"] = {"value": 1.0 / s32, "unit": "spectra/s", "seconds_per_spectrum": s32,
+                   "omega_finite_positive": bool(np.all(np.isfinite(om)) and np.all(om > 0)),
+                   "kernels": {k: {"ms": prof[k]["ms"], "launches": prof[k]["launches"],
+                                   "GBps": prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9 if prof[k]["ms"] > 0 else None,
+                                   "frac_of_peak": (prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"])
+                                   if prof[k]["ms"] > 0 else None}
+                               for k in sigw.KINDS if prof[k]["launches"]},
+                   "path_fraction": path_fraction(spec.N, 1.0 / s32, peaks["hbm_gbs"])}
+    shells = np.array([1, 86, 171, 256], dtype=np.int32)
+    with sigw.Plan(spec.N, spec.L, stream=stream.cuda_stream, precision=64, max_batch=1) as p:
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        p.generate_spec(spec)
+        b.record(stream)
+        p.spectrum_async(dev_out.data_ptr(), shells)
+        c.record(stream)
+        c.synchronize()
+        gen, sh = a.elapsed_time(b) / 1e3, b.elapsed_time(c) / 1e3
+    s64 = gen + sh * n_sh / len(shells)
+    out["fp64"] = {"value": 1.0 / s64, "unit": "spectra/s", "seconds_per_spectrum": s64,
+                   "sample": "synthesis + shells %s timed, extrapolated to all %d shells (sampled)" % (
+                       shells.tolist(), n_sh)}
+    out["fp32_over_fp64"] = s64 / s32
+    return out
+
+
+def path_fraction(N, spectra_per_s, peak_gbs):
+    """The whole path against the algorithmic byte count of the method: 312 field-FFTs per target shell
+    (2 kernels x (3 x 50 inverse + 6 forward)), N/2 shells per spectrum, each field-FFT reading and writing one
+    FP32 field once (4 N^3 real + 8 N^2 (N/2 + 1) half-complex bytes)."""
+    per_fft = 4.0 * N ** 3 + 8.0 * N * N * (N // 2 + 1)
+    per_spec = 312.0 * (N // 2) * per_fft
+    achieved = per_spec * spectra_per_s / 1e9
+    return {"bytes_per_spectrum": per_spec, "achieved_GBps": achieved, "peak_GBps": peak_gbs,
+            "frac": achieved / peak_gbs}
 
 
 def fft_crosscheck(N=256, reps=10):
@@ -419,7 +536,7 @@ def run_reference(args):
             vals.append(r)
     v = statistics.mean(x["value"] for x in vals)
     wall = time.perf_counter() - t_start
-    line = {"impl": "reference", "metric": "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "spectra/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / (args.warmup + args.steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox noise, log-normal P_zeta, USR map)",
@@ -440,7 +557,9 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--n-alpha", type=int, default=50, help="separable terms kept (the paper's 50; fewer only to "
                     "shrink a profiling run)")
-    ap.add_argument("--fp64-shells", type=int, default=4)
+    ap.add_argument("--fp64-spectrum", type=int, default=1, help="time one full FP64 spectrum (0: skip)")
+    ap.add_argument("--broad512", type=int, default=1, help="run the 512^3 leg (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
     ap.add_argument("--cpu-terms", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paper-scan", action="store_true")
@@ -448,8 +567,12 @@ def main():
                     help="separable terms per strided-pass launch (0: chosen by the autotuner)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64],
                     help="working precision of the main leg (64 only for profiling the FP64 path)")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests per load (0: no serving legs)")
+    ap.add_argument("--serve-loads", default="0.5,0.8,1.0", help="loads as fractions of the measured capacity")
+    ap.add_argument("--serve-sizes", default="64,128,256")
+    ap.add_argument("--serve-fp64-requests", type=int, default=60, help="FP64 serving requests (0: no FP64 leg)")
+    ap.add_argument("--serve-fp64-sizes", default="64,128")
+    ap.add_argument("--serve-fp64-load", type=float, default=0.8)
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-batch", type=int, default=4)
     ap.add_argument("--serve-express", type=int, default=1, help="express slots for small lattices (0: none)")
