@@ -241,12 +241,10 @@ sigw_status sigw_server_destroy(sigw_server srv);
  * n_alpha; exactly opts->alpha_batch when that is set) and, where two exist (FP32, N >= 128), both radix
  * variants of the strided passes.  Keeps the fastest in the plan and in a process-wide table keyed by
  * (N, precision, max_batch, n_alpha) from which later plans with alpha_batch = 0 start; then times both radix
- * forms of the last inverse pass (FP32, N = 128, 256, 512) on the terms just produced, and, where it exists (FP32,
- * N = 256), the first and second inverse passes fused in one cluster kernel with the last pass reading its
- * swizzled tiles, against the best unfused choice.  An untuned FP32 plan starts from the bits these runs chose
- * on GB300 (2 from N = 128, 7 at N = 512).  Outputs nullable: chosen
+ * forms of the last inverse pass (FP32, N = 128, 256, 512) on the terms just produced.  An untuned FP32 plan starts
+ * from the bits these runs chose on GB300 (2 from N = 128, 7 at N = 512).  Outputs nullable: chosen
  * terms per launch, variant bits (1: alternative radix of the first strided pass, 2: radix-16 last pass,
- * 4: alternative radix of the second strided pass, 8: fused first and second passes) and the time in ms of the
+ * 4: alternative radix of the second strided pass) and the time in ms of the
  * chosen strided passes plus last pass for one kernel (m = s).  Waits for the stream.
  * Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */
 sigw_status sigw_plan_autotune(sigw_plan plan, int n_c, int* out_alpha_batch, int* out_variant, double* out_ms);
@@ -258,9 +256,8 @@ sigw_status sigw_plan_set_tuning(sigw_plan plan, int alpha_batch, int variant);
 
 /* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter,
  * gradient), 2 second inverse pass, 3 last inverse pass + product + first forward pass, 4 second forward
- * pass, 5 last forward pass + TT projection + shell sum, 6 bin finalisation, 7 first and second inverse
- * passes fused (variant bit 8). */
-#define SIGW_NKINDS 8
+ * pass, 5 last forward pass + TT projection + shell sum, 6 bin finalisation. */
+#define SIGW_NKINDS 7
 typedef struct sigw_profile {
   double ms[SIGW_NKINDS];        /* summed CUDA-event durations (only while event timing is on) */
   double bytes[SIGW_NKINDS];     /* algorithmic bytes: each input element read once, each output written once */

@@ -14,8 +14,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 #include "fft.cuh"
 #include "ops.h"
 
@@ -575,25 +573,8 @@ template <typename T, int N> struct AltP3 {
 // row[k] or conj(row[N-k]); grad: i n^D(k) times the plain value, zero at k = 0 and k = N/2.
 // With P E = N, k < N/2 exactly when r < E/2, so only j = 0 needs a run-time test (k = 0 and k = N/2 come from
 // the packed column 0), and the wave number of the gradient is (T) j plus a compile-time offset.
-// A row of a bulk-copied tile of RPC rows x N/2 packed columns, in shared memory.  Plain tiles are row-major; the
-// swizzled tiles written by the fused first/second pass (16 rows) store each column's 16 rows as eight 16-byte
-// chunks of two rows in the order (rr / 2) xor (c mod 8), so that one row read across c hits distinct banks.
-template <typename T, int H>
-struct PlainRow {
-  const cx<T>* p;  // the row's first element
-  __device__ __forceinline__ cx<T> operator[](int k) const { return p[k]; }
-};
-template <typename T>
-struct SwzRow {
-  const cx<T>* tile;  // the tile's first element
-  int rr;             // row within the 16-row tile
-  __device__ __forceinline__ cx<T> operator[](int k) const {
-    return tile[(((k << 3) + ((rr >> 1) ^ (k & 7))) << 1) + (rr & 1)];
-  }
-};
-
-template <typename T, int N, int E, typename Row>
-__device__ __forceinline__ cx<T> herm_plain_r(const Row& row, int j, int r) {
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_plain_r(const cx<T>* row, int j, int r) {
   constexpr int P = N / E;
   if (r < E / 2) {
     const cx<T> v = row[j + r * P];
@@ -603,8 +584,8 @@ __device__ __forceinline__ cx<T> herm_plain_r(const Row& row, int j, int r) {
   const cx<T> v = row[hz ? 0 : (E - r) * P - j];
   return hz ? mk<T>(v.y, (T)0) : conjg<T>(v);
 }
-template <typename T, int N, int E, typename Row>
-__device__ __forceinline__ cx<T> herm_grad_r(const Row& row, int j, int r, T fj) {
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_grad_r(const cx<T>* row, int j, int r, T fj) {
   constexpr int P = N / E;
   if (r < E / 2) {
     const cx<T> x = row[j + r * P];
@@ -619,8 +600,8 @@ __device__ __forceinline__ cx<T> herm_grad_r(const Row& row, int j, int r, T fj)
 
 // The same values by a run-time test on k = j + r P.  At N = 512 this form measured faster in the radix-16 last
 // pass (the specialised form above costs registers there, where the kernel already spills).
-template <typename T, int N, int E, typename Row>
-__device__ __forceinline__ cx<T> herm_plain_k(const Row& row, int j, int r) {
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_plain_k(const cx<T>* row, int j, int r) {
   constexpr int H = N / 2;
   const int k = j + r * (N / E);
   if (k == 0) return mk<T>(row[0].x, (T)0);
@@ -628,8 +609,8 @@ __device__ __forceinline__ cx<T> herm_plain_k(const Row& row, int j, int r) {
   if (k < H) return row[k];
   return conjg<T>(row[N - k]);
 }
-template <typename T, int N, int E, typename Row>
-__device__ __forceinline__ cx<T> herm_grad_k(const Row& row, int j, int r) {
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> herm_grad_k(const cx<T>* row, int j, int r) {
   constexpr int H = N / 2;
   const int k = j + r * (N / E);
   if (k == 0 || k == H) return mk<T>((T)0, (T)0);
@@ -644,13 +625,13 @@ __device__ __forceinline__ cx<T> herm_grad_k(const Row& row, int j, int r) {
   }
   return mk<T>(-n * x.y, n * x.x);
 }
-template <typename T, int N, int E, typename Row>
-__device__ __forceinline__ cx<T> row_plain(const Row& row, int j, int r) {
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> row_plain(const cx<T>* row, int j, int r) {
   if constexpr (N <= 256) return herm_plain_r<T, N, E>(row, j, r);
   else return herm_plain_k<T, N, E>(row, j, r);
 }
-template <typename T, int N, int E, typename Row>
-__device__ __forceinline__ cx<T> row_grad(const Row& row, int j, int r, T fj) {
+template <typename T, int N, int E>
+__device__ __forceinline__ cx<T> row_grad(const cx<T>* row, int j, int r, T fj) {
   if constexpr (N <= 256) return herm_grad_r<T, N, E>(row, j, r, fj);
   else return herm_grad_k<T, N, E>(row, j, r);
 }
@@ -688,8 +669,7 @@ __device__ __forceinline__ void accum6<float, true>(float sa, float g0, float2 z
 // A thread whose wait gave up sets *err, stops waiting and (thread 0) stops issuing copies; before the CTA exits,
 // thread 0 waits, with the default limit, for the last copy issued into each stage, so no bulk copy can still be
 // writing into the CTA's shared memory after it has exited.  The results of a launch that set *err are invalid.
-// SWZ: W holds the swizzled 16-row tiles of the fused first/second pass (FP32, 16 rows per CTA) instead of plain rows.
-template <typename T, int N, int E_ = ((N >= 16) ? 8 : 4), bool SWZ = false>
+template <typename T, int N, int E_ = ((N >= 16) ? 8 : 4)>
 __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>* __restrict__ W,
                                                                    const T* __restrict__ sigma, int n_alpha,
                                                                    cx<T>* __restrict__ F, int n_c,
@@ -697,8 +677,6 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
                                                                    int* __restrict__ err, long long wait_limit) {
   using CF = P3Cfg<T, N, E_>;
   constexpr int E = CF::E, P = CF::P, H = N / 2, RPC = CF::RPC, STAGES = CF::STAGES;
-  static_assert(!SWZ || (RPC == 16 && sizeof(T) == 4), "swizzled tiles hold 16 FP32 rows");
-  using Row = typename std::conditional<SWZ, SwzRow<T>, PlainRow<T, H>>::type;
   using Sync = typename RowSync<P>::type;
   using Lay = typename CF::Lay;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -751,12 +729,13 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
     if (ok) ok = mbar_wait(bars + s, (uint32_t)((pr / STAGES) & 1), err, wait_limit);
     const int a = 2 * pr;
     const bool two = a + 1 < n_alpha;
-    const cx<T>* st = ring + s * CF::STAGE_ELEMS;
-    auto row_of = [&](int f) {
-      if constexpr (SWZ) return SwzRow<T>{st + f * RPC * H, rr};
-      else return PlainRow<T, H>{st + f * RPC * H + rr * H};
-    };
-    const Row wb0 = row_of(0), w10 = row_of(1), w20 = row_of(2), wb1 = row_of(3), w11 = row_of(4), w21 = row_of(5);
+    const cx<T>* st = ring + s * CF::STAGE_ELEMS + rr * H;
+    const cx<T>* wb0 = st;
+    const cx<T>* w10 = st + RPC * H;
+    const cx<T>* w20 = st + 2 * RPC * H;
+    const cx<T>* wb1 = st + 3 * RPC * H;
+    const cx<T>* w11 = st + 4 * RPC * H;
+    const cx<T>* w21 = st + 5 * RPC * H;
     // (g0^a + i g0^{a+1}) first; its two real parts are kept while the other two transforms run
     cx<T> zB[E], z[E];
 #pragma unroll

@@ -109,11 +109,11 @@ struct OpsT {
     }
     return p2_v<N, SH::ES, SH::TC>(Ta, Tb, W, n_alpha, alpha0, nb, batch, tw, st);
   }
-  template <int N, int E, bool SWZ = false>
+  template <int N, int E>
   static cudaError_t p3_v(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
                           int* err, long long wait_limit, cudaStream_t st) {
     using CF = P3Cfg<T, N, E>;
-    auto k = k_p3<T, N, E, SWZ>;
+    auto k = k_p3<T, N, E>;
     SIGW_CHECK_LAUNCH(allow_smem(k, CF::SMEM));
     dim3 grid((N * N) / CF::RPC, batch);
     k<<<grid, CF::THREADS, CF::SMEM, st>>>((const C*)W, (const T*)sigma, n_alpha, (C*)F, n_c, (const C*)tw, err,
@@ -124,9 +124,6 @@ struct OpsT {
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
                           int* err, long long wait_limit, int variant, cudaStream_t st) {
     if constexpr (AltP3<T, N>::exists) {
-      if constexpr (sizeof(T) == 4 && N == 256) {  // tiles of the fused first/second pass
-        if (variant & 8) return p3_v<N, 16, true>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
-      }
       if (variant & 2) return p3_v<N, AltP3<T, N>::E>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
     }
     return p3_v<N, ((N >= 16) ? 8 : 4)>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
