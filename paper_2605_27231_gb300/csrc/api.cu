@@ -1083,12 +1083,14 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
         if (e != cudaSuccess) status = cuda_fail(p, e, "autotune launch");
       }
     }
-    float t3[2] = {1e30f, 1e30f};
-    for (int v3 = 0; v3 < 2 && status == SIGW_OK; ++v3) {
+    const int np3 = OPS(p, p3_variants, N);  // 2: radix 8 / 16; 3: also radix 16 with TMEM accumulators
+    const int p3bits[3] = {0, 2, 8};
+    float t3[3] = {1e30f, 1e30f, 1e30f};
+    for (int v3 = 0; v3 < np3 && status == SIGW_OK; ++v3) {
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, st);
         cudaError_t e = OPS(p, p3, N, p->d_work, p->d_sigma[0], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err,
-                            sigw::kDefaultWaitLimit, v3 ? 2 : 0, st);
+                            sigw::kDefaultWaitLimit, p3bits[v3], st);
         cudaEventRecord(e1, st);
         if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&t3[v3], e0, e1) != cudaSuccess) {
@@ -1097,8 +1099,13 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
         }
       }
     }
-    if (status == SIGW_OK && t3[1] < t3[0]) bestP3 = 2;
-    if (status == SIGW_OK) best += std::min(t3[0], t3[1]);
+    int bv = 0;
+    for (int v3 = 1; v3 < np3; ++v3)
+      if (t3[v3] < t3[bv]) bv = v3;
+    if (status == SIGW_OK) {
+      bestP3 = p3bits[bv];
+      best += t3[bv];
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1180,7 +1187,7 @@ sigw_status sigw_target_scan(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap
 
 sigw_status sigw_plan_set_tuning(sigw_plan p, int alpha_batch, int variant) {
   if (!p) return SIGW_EINVAL;
-  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 7)
+  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 15)
     return fail(p, SIGW_EINVAL, "sigw_plan_set_tuning: alpha_batch or variant out of range");
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
   CKP(p, cudaStreamSynchronize(p->st), "set_tuning");

@@ -800,6 +800,212 @@ __global__ void __launch_bounds__(P3Cfg<T, N, E_>::THREADS, 1) k_p3(const cx<T>*
   }
 }
 
+// ---------------------------------------------------------------- tensor memory (TMEM) helpers
+// A CTA allocates NCOLS 32-bit columns of the SM's tensor memory (128 lanes x 512 columns) with one warp, keeps
+// per-thread values in its own lane (warp w may access lanes 32 (w mod 4) .. 32 (w mod 4) + 31), and frees them
+// with the same warp before it exits.  No tensor-core instruction is involved: the memory is used as storage.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {  // whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 16 consecutive columns of this thread's lane into registers; the load and its completion wait are one
+// statement, so no use of the values can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// P3 with its accumulators in tensor memory (autotuner variant bit 8; FP32, radix 16, N = 256).  The last pass
+// above keeps the six product components of its 16 points per thread in registers (96 of its 254), which holds
+// it to one CTA of 8 warps per SM.  Here they live in TMEM (columns 16 c .. 16 c + 15 of the thread's lane for
+// component c = s00, s11, s22, s01, s02, s12), so a thread needs ~170 registers and three CTAs of 8 rows (4 warps)
+// share an SM.  One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the
+// stage is refilled for the next pair while the transforms run, and the other CTAs of the SM cover the copy.
+// Bounded waits, error flag and the drain before exit as in k_p3.
+template <int N>
+struct P3TCfg {
+  static constexpr int H = N / 2, E = 16, P = N / E, RPC = 8, THREADS = RPC * P;
+  static_assert(THREADS == 128, "one warp per TMEM lane quarter");
+  using Lay = RowLayout<float, N, true, 4>;
+  static constexpr int STAGE_ELEMS = 6 * RPC * H;  // three fields of two terms
+  static constexpr uint32_t NCOLS = 128;           // TMEM columns per CTA (96 used)
+  static constexpr size_t SMEM = (size_t)STAGE_ELEMS * 8 + (size_t)RPC * Lay::SIZE * 8 + 16;
+};
+
+template <int N>
+__global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* __restrict__ W,
+                                                                  const float* __restrict__ sigma, int n_alpha,
+                                                                  float2* __restrict__ F, int n_c,
+                                                                  const float2* __restrict__ tw,
+                                                                  int* __restrict__ err, long long wait_limit) {
+  using CF = P3TCfg<N>;
+  constexpr int E = CF::E, P = CF::P, H = CF::H, RPC = CF::RPC;
+  using Sync = typename RowSync<P>::type;
+  using Lay = typename CF::Lay;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float2* ring = reinterpret_cast<float2*>(smraw);
+  float2* xch = ring + CF::STAGE_ELEMS;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + RPC * Lay::SIZE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int rr = threadIdx.x / P, j = threadIdx.x % P;
+  const Lay L{xch + rr * Lay::SIZE};
+  const long row0 = (long)blockIdx.x * RPC;
+  const long row = row0 + rr;
+  const int b = blockIdx.y;
+  const long fstride = (long)N * N * H;
+  const int npairs = (n_alpha + 1) / 2;
+  constexpr uint32_t COPY = RPC * H * sizeof(float2);
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tmem_alloc(tslot, CF::NCOLS);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tbase = *tslot + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lane quarter
+  auto tcol = [&](int c) { return tbase + (uint32_t)(16 * c); };
+  {
+    float z0[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z0[i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tmem_st16(tcol(c), z0);
+    tmem_wait_st();
+  }
+  auto issue = [&](int pr) {  // thread 0: the six row blocks of term pair pr into the stage
+    const int a = 2 * pr;
+    const bool two = a + 1 < n_alpha;
+    fence_proxy_async();
+    mbar_expect_tx(bar, (two ? 6u : 3u) * COPY);
+    for (int f = 0; f < 3; ++f) {
+      bulk_g2s(ring + f * RPC * H, W + (((long)b * 3 + f) * n_alpha + a) * fstride + row0 * H, COPY, bar);
+      if (two) bulk_g2s(ring + (3 + f) * RPC * H, W + (((long)b * 3 + f) * n_alpha + a + 1) * fstride + row0 * H, COPY,
+                        bar);
+    }
+  };
+  if (threadIdx.x == 0) issue(0);
+  int issued = 1;  // term pairs whose copies thread 0 has issued
+  const float fj = (float)j;
+  bool ok = true;
+  for (int pr = 0; pr < npairs; ++pr) {
+    if (ok) ok = mbar_wait(bar, (uint32_t)(pr & 1), err, wait_limit);
+    const int a = 2 * pr;
+    const bool two = a + 1 < n_alpha;
+    const float2* wb0 = ring + rr * H;
+    const float2* w10 = wb0 + RPC * H;
+    const float2* w20 = wb0 + 2 * RPC * H;
+    const float2* wb1 = wb0 + 3 * RPC * H;
+    const float2* w11 = wb0 + 4 * RPC * H;
+    const float2* w21 = wb0 + 5 * RPC * H;
+    // inputs of the three transforms: (g0^a + i g0^{a+1}), (g2^a + i g1^a), (g2^{a+1} + i g1^{a+1})
+    float2 zB[E], za[E], zb[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const float2 g0 = row_plain<float, N, E>(w20, j, r);
+      const float2 g0b = two ? row_plain<float, N, E>(w21, j, r) : make_float2(0.f, 0.f);
+      zB[r] = make_float2(g0.x - g0b.y, g0.y + g0b.x);
+      const float2 g2 = row_grad<float, N, E>(wb0, j, r, fj), g1 = row_plain<float, N, E>(w10, j, r);
+      za[r] = make_float2(g2.x - g1.y, g2.y + g1.x);
+      if (two) {
+        const float2 h2 = row_grad<float, N, E>(wb1, j, r, fj), h1 = row_plain<float, N, E>(w11, j, r);
+        zb[r] = make_float2(h2.x - h1.y, h2.y + h1.x);
+      } else {
+        zb[r] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();  // the stage has been read: refill it for the next pair while the transforms run
+    if (threadIdx.x == 0 && ok && pr + 1 < npairs) {
+      issue(pr + 1);
+      issued = pr + 2;
+    }
+    fft_pencil<float, N, E, +1, Lay, Sync>(zB, j, L, tw, Sync());
+    fft_pencil<float, N, E, +1, Lay, Sync>(za, j, L, tw, Sync());
+    fft_pencil<float, N, E, +1, Lay, Sync>(zb, j, L, tw, Sync());
+    const float sa = sigma[a], sb = two ? sigma[a + 1] : 0.f;
+    // s00 += sa g0a^2 + sb g0b^2; s11 += sa g1a^2 + sb g1b^2; s22 likewise with g2; s01, s02, s12 the cross terms
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      tmem_ld16(tcol(c), acc);
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const float g0a = zB[r].x, g0b = zB[r].y, g2a = za[r].x, g1a = za[r].y, g2b = zb[r].x, g1b = zb[r].y;
+        float pa, qa, pb, qb;
+        if (c == 0) { pa = g0a; qa = g0a; pb = g0b; qb = g0b; }
+        else if (c == 1) { pa = g1a; qa = g1a; pb = g1b; qb = g1b; }
+        else if (c == 2) { pa = g2a; qa = g2a; pb = g2b; qb = g2b; }
+        else if (c == 3) { pa = g0a; qa = g1a; pb = g0b; qb = g1b; }
+        else if (c == 4) { pa = g0a; qa = g2a; pb = g0b; qb = g2b; }
+        else { pa = g1a; qa = g2a; pb = g1b; qb = g2b; }
+        acc[r] = fmaf(sb * pb, qb, fmaf(sa * pa, qa, acc[r]));
+      }
+      tmem_st16(tcol(c), acc);
+    }
+    tmem_wait_st();
+  }
+  if (threadIdx.x == 0 && issued > 0) mbar_wait(bar, (uint32_t)((issued - 1) & 1), err);  // drain the last copy
+  // forward R2C of the six real rows, two per complex transform: (s00, s11), (s22, s01), (s02, s12)
+  float2* zo = L.buf(0);
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) {
+    float u[16], w[16];
+    tmem_ld16(tcol(2 * q), u);
+    tmem_ld16(tcol(2 * q + 1), w);
+    float2 z[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) z[r] = make_float2(u[r], w[r]);
+    fft_pencil<float, N, E, -1, Lay, Sync>(z, j, L, tw, Sync());
+#pragma unroll
+    for (int r = 0; r < E; ++r) zo[L.idx(j + r * P)] = z[r];
+    Sync()();
+    const int ncp = n_c + 1;
+    const int c1 = q == 0 ? 0 : (q == 1 ? 2 : 4), c2 = q == 0 ? 1 : (q == 1 ? 3 : 5);
+    // stored component order of F: (00, 11, 22, 01, 02, 12) = c = 0..5
+    float2* f1 = F + (((long)b * 6 + c1) * N * N + row) * ncp;
+    float2* f2 = F + (((long)b * 6 + c2) * N * N + row) * ncp;
+    for (int k = j; k <= n_c; k += P) {
+      const float2 zk = zo[L.idx(k)];
+      const float2 zm = conjg<float>(zo[L.idx((N - k) & (N - 1))]);
+      f1[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+      f2[k] = make_float2(0.5f * (zk.y - zm.y), -0.5f * (zk.x - zm.x));
+    }
+    Sync()();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(*tslot, CF::NCOLS);
+}
+
 // F2: forward DFT along axis 1 of F[b][comp][a0][a1][k2] (k2 = 0..n_c), keeping n1 in [n1lo, n1lo + nk1).
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_f2(const cx<T>* __restrict__ F, cx<T>* __restrict__ F2, int n_c, int n1lo,

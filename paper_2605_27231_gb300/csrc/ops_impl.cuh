@@ -121,8 +121,22 @@ struct OpsT {
     return cudaGetLastError();
   }
   template <int N>
+  static cudaError_t p3_tm_v(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
+                             const void* tw, int* err, long long wait_limit, cudaStream_t st) {
+    using CF = P3TCfg<N>;
+    auto k = k_p3_tm<N>;
+    SIGW_CHECK_LAUNCH(allow_smem(k, CF::SMEM));
+    dim3 grid((N * N) / CF::RPC, batch);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>((const float2*)W, (const float*)sigma, n_alpha, (float2*)F, n_c,
+                                           (const float2*)tw, err, wait_limit);
+    return cudaGetLastError();
+  }
+  template <int N>
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
                           int* err, long long wait_limit, int variant, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4 && N == 256) {  // accumulators in tensor memory
+      if (variant & 8) return p3_tm_v<N>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
+    }
     if constexpr (AltP3<T, N>::exists) {
       if (variant & 2) return p3_v<N, AltP3<T, N>::E>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
     }
@@ -260,7 +274,7 @@ int OpsRT<T>::rows_blocks(int N) {
 template <typename T>
 int OpsRT<T>::p3_variants(int N) {
   if (N == 128) return AltP3<T, 128>::exists ? 2 : 1;
-  if (N == 256) return AltP3<T, 256>::exists ? 2 : 1;
+  if (N == 256) return AltP3<T, 256>::exists ? (sizeof(T) == 4 ? 3 : 2) : 1;
   if (N == 512) return AltP3<T, 512>::exists ? 2 : 1;
   return 1;
 }

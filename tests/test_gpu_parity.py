@@ -256,6 +256,27 @@ def test_bulk_copy_wait_timeout_is_reported_and_recoverable(lib, dec, N):
             assert np.array_equal(p.spectrum()["omega"][0], first)
 
 
+def test_tensor_memory_last_pass_wait_timeout_and_recovery(lib):
+    """The last pass with its accumulators in tensor memory (variant bit 8, 256^3): its bounded waits given a
+    one-cycle limit report SIGW_ETIMEOUT, after which the same plan gives the bits it gives without the hook, and
+    the same values as the register-accumulator form within FP32 round-off."""
+    spec = workloads.Spec(N=256, L=1.0, A=1e-2, sigma=0.5, kstar=32 * 2 * np.pi, kind="local", F_NL=2.0, seed=29)
+    shells = [5, 77]
+    with lib.Plan(256, 1.0, precision=32, n_alpha=6) as p:
+        p.generate_spec(spec)
+        p.set_tuning(6, 2)
+        regs = p.spectrum(shells)["omega"][0]
+        p.set_tuning(6, 8)
+        clean = p.spectrum(shells)["omega"][0]
+        p.debug_wait_limit(1)
+        with pytest.raises(lib.SigwError) as e:
+            p.spectrum(shells)
+        assert e.value.status == lib.ETIMEOUT
+        p.debug_wait_limit(0)
+        assert np.array_equal(p.spectrum(shells)["omega"][0], clean)
+    np.testing.assert_allclose(clean, regs, rtol=2e-6)
+
+
 def test_usr_strict_mode(lib):
     spec = workloads.Spec(N=16, L=1.0, A=5e-1, sigma=0.5, kstar=4 * 2 * np.pi, kind="usr", seed=2)
     with lib.Plan(16, 1.0, n_alpha=2, strict_domain=1, precision=64) as p:
@@ -381,14 +402,15 @@ def test_graph_replay_equals_direct_launches(lib):
 
 @pytest.mark.parametrize("N", [128, 256])
 def test_every_variant_matches_oracle(lib, dec, N):
-    """Each radix variant (bits 1, 2, 4 and all together) on sampled shells of a local-map field, vs the oracle."""
+    """Each radix variant (bits 1, 2, 4 and all together; at 256^3 also the last pass with its accumulators in tensor
+    memory, bit 8) on sampled shells of a local-map field, vs the oracle."""
     spec = workloads.scaled(workloads.workload("local128"), N)
     shells = [3, N // 4]
     d10 = odec.build(n_alpha=10)
     ref, _, _ = _oracle(spec, d10, shells)
     with lib.Plan(N, spec.L, precision=32, n_alpha=10) as p:
         p.generate_spec(spec)
-        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)):
+        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)) + (((10, 8), (4, 15)) if N == 256 else ()):
             p.set_tuning(B, v)
             np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
         with pytest.raises(lib.SigwError):
