@@ -430,9 +430,10 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
   p->L = L;
   p->opts = o;
   p->B = auto_alpha_batch(o);
-  // Untuned default: the radices the autotuner chose on GB300 at usr256 and broad512 (radix-16 last pass from
-  // 128^3; at 512^3 also the 512-specific strided passes).  sigw_plan_autotune or the table may override it.
-  p->variant = o.precision == 32 ? (N == 512 ? 7 : (N >= 128 ? 2 : 0)) : 0;
+  // Untuned default: the choices the autotuner made on GB300 at usr256 and broad512 (radix-16 last pass from
+  // 128^3; at 256^3 the first and last passes with their per-thread state in tensor memory; at 512^3 the
+  // 512-specific strided passes).  sigw_plan_autotune or the table may override it.
+  p->variant = o.precision == 32 ? (N == 512 ? 7 : (N == 256 ? 26 : (N >= 128 ? 2 : 0))) : 0;
   std::string e;
   if (!sigw::build_decomposition(params_of(o), &p->dec, &e)) {
     delete p;
@@ -1029,7 +1030,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
   CKP(p, cudaEventCreate(&e0), "event");
   CKP(p, cudaEventCreate(&e1), "event");
   double best = 1e300;
-  int bestB = p->B, bestV = p->variant & 5;
+  int bestB = p->B, bestV = p->variant & 21;
   const int cands[] = {4, 5, 8, 10, 16};
   sigw_status status = SIGW_OK;
   // For each terms-per-launch candidate the two strided passes are timed separately (each with both radix
@@ -1052,21 +1053,29 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
     }
     return SIGW_OK;
   };
+  // first-pass candidates: the two radix forms and, where it exists, the radix-16 form with its tile in TMEM
+  const bool p1tm = p->opts.precision == 32 && N == 256;
+  const int p1bits[3] = {0, 1, 16};
+  const int np1 = nvar + (p1tm ? 1 : 0);
   for (int B : cands) {
     if (p->opts.alpha_batch > 0) B = bmax;  // terms per launch fixed by the options: tune the radices only
     if (B > bmax || status != SIGW_OK) continue;
-    float t1[2] = {1e30f, 1e30f}, t2[2] = {1e30f, 1e30f};
-    for (int v = 0; v < nvar && status == SIGW_OK; ++v) {
-      status = time_pass(0, B, v, &t1[v]);  // P1 writes the T that P2 reads next
-      if (status == SIGW_OK) status = time_pass(1, B, v, &t2[v]);
+    float t1[3] = {1e30f, 1e30f, 1e30f}, t2[2] = {1e30f, 1e30f};
+    for (int v = 0; v < np1 && status == SIGW_OK; ++v) {
+      const int bits = (v == nvar) ? 16 : p1bits[v];
+      status = time_pass(0, B, bits, &t1[v]);  // P1 writes the T that P2 reads next
+      if (status == SIGW_OK && v < nvar) status = time_pass(1, B, v, &t2[v]);
     }
     if (status != SIGW_OK) break;
-    const int v1 = t1[1] < t1[0] ? 1 : 0, v2 = t2[1] < t2[0] ? 1 : 0;
+    int v1 = 0;
+    for (int v = 1; v < np1; ++v)
+      if (t1[v] < t1[v1]) v1 = v;
+    const int v2 = t2[1] < t2[0] ? 1 : 0;
     const double ms = (double)t1[v1] + (double)t2[v2];
     if (ms < best) {
       best = ms;
       bestB = B;
-      bestV = v1 | (v2 << 2);
+      bestV = (v1 == nvar ? 16 : p1bits[v1]) | (v2 << 2);
     }
     if (p->opts.alpha_batch > 0) break;
   }
@@ -1187,7 +1196,7 @@ sigw_status sigw_target_scan(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap
 
 sigw_status sigw_plan_set_tuning(sigw_plan p, int alpha_batch, int variant) {
   if (!p) return SIGW_EINVAL;
-  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 15)
+  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 31)
     return fail(p, SIGW_EINVAL, "sigw_plan_set_tuning: alpha_batch or variant out of range");
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
   CKP(p, cudaStreamSynchronize(p->st), "set_tuning");

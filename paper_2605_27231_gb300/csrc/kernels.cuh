@@ -844,9 +844,9 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // P3 with its accumulators in tensor memory (autotuner variant bit 8; FP32, radix 16, N = 256).  The last pass
 // above keeps the six product components of its 16 points per thread in registers (96 of its 254), which holds
-// it to one CTA of 8 warps per SM.  Here they live in TMEM (columns 16 c .. 16 c + 15 of the thread's lane for
-// component c = s00, s11, s22, s01, s02, s12), so a thread needs ~170 registers and three CTAs of 8 rows (4 warps)
-// share an SM.  One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the
+// it to one CTA of 8 warps per SM.  Here they live in TMEM, in the thread's lane: s00 in columns 0-15, s12 in
+// 16-31, (s22, s11) interleaved in 32-63 and (s02, s01) interleaved in 64-95, so a thread needs ~170 registers and
+// three CTAs of 8 rows (4 warps) share an SM.  One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the
 // stage is refilled for the next pair while the transforms run, and the other CTAs of the SM cover the copy.
 // Bounded waits, error flag and the drain before exit as in k_p3.
 template <int N>
@@ -951,24 +951,41 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
     fft_pencil<float, N, E, +1, Lay, Sync>(za, j, L, tw, Sync());
     fft_pencil<float, N, E, +1, Lay, Sync>(zb, j, L, tw, Sync());
     const float sa = sigma[a], sb = two ? sigma[a + 1] : 0.f;
-    // s00 += sa g0a^2 + sb g0b^2; s11 += sa g1a^2 + sb g1b^2; s22 likewise with g2; s01, s02, s12 the cross terms
-    float acc[16];
+    // za = (g2a, g1a), zb = (g2b, g1b), zB = (g0a, g0b).  Chunks: s00 and s12 (16 columns each), (s22, s11) and
+    // (s02, s01) interleaved (32 columns each), so the pair updates are paired (FP32x2) multiply-adds.
+    {
+      float u[16];
+      tmem_ld16(tcol(0), u);  // s00 += sa g0a^2 + sb g0b^2
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      tmem_ld16(tcol(c), acc);
+      for (int r = 0; r < E; ++r) u[r] = fmaf(sb * zB[r].y, zB[r].y, fmaf(sa * zB[r].x, zB[r].x, u[r]));
+      tmem_st16(tcol(0), u);
+      tmem_ld16(tcol(1), u);  // s12 += sa g1a g2a + sb g1b g2b
 #pragma unroll
-      for (int r = 0; r < E; ++r) {
-        const float g0a = zB[r].x, g0b = zB[r].y, g2a = za[r].x, g1a = za[r].y, g2b = zb[r].x, g1b = zb[r].y;
-        float pa, qa, pb, qb;
-        if (c == 0) { pa = g0a; qa = g0a; pb = g0b; qb = g0b; }
-        else if (c == 1) { pa = g1a; qa = g1a; pb = g1b; qb = g1b; }
-        else if (c == 2) { pa = g2a; qa = g2a; pb = g2b; qb = g2b; }
-        else if (c == 3) { pa = g0a; qa = g1a; pb = g0b; qb = g1b; }
-        else if (c == 4) { pa = g0a; qa = g2a; pb = g0b; qb = g2b; }
-        else { pa = g1a; qa = g2a; pb = g1b; qb = g2b; }
-        acc[r] = fmaf(sb * pb, qb, fmaf(sa * pa, qa, acc[r]));
+      for (int r = 0; r < E; ++r) u[r] = fmaf(sb * zb[r].y, zb[r].x, fmaf(sa * za[r].y, za[r].x, u[r]));
+      tmem_st16(tcol(1), u);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // points 8 h .. 8 h + 7 of the interleaved chunks
+      float u[16], w[16];
+      tmem_ld16(tcol(2) + 16 * h, u);  // (s22, s11) += sa (g2a, g1a)^2 + sb (g2b, g1b)^2
+      tmem_ld16(tcol(4) + 16 * h, w);  // (s02, s01) += sa g0a (g2a, g1a) + sb g0b (g2b, g1b)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = 8 * h + i;
+        float2 c = make_float2(u[2 * i], u[2 * i + 1]);
+        c = __ffma2_rn(__fmul2_rn(za[r], make_float2(sa, sa)), za[r], c);
+        c = __ffma2_rn(__fmul2_rn(zb[r], make_float2(sb, sb)), zb[r], c);
+        u[2 * i] = c.x;
+        u[2 * i + 1] = c.y;
+        float2 d = make_float2(w[2 * i], w[2 * i + 1]);
+        const float t0a = sa * zB[r].x, t0b = sb * zB[r].y;
+        d = __ffma2_rn(make_float2(t0a, t0a), za[r], d);
+        d = __ffma2_rn(make_float2(t0b, t0b), zb[r], d);
+        w[2 * i] = d.x;
+        w[2 * i + 1] = d.y;
       }
-      tmem_st16(tcol(c), acc);
+      tmem_st16(tcol(2) + 16 * h, u);
+      tmem_st16(tcol(4) + 16 * h, w);
     }
     tmem_wait_st();
   }
@@ -977,12 +994,39 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
   float2* zo = L.buf(0);
 #pragma unroll 1
   for (int q = 0; q < 3; ++q) {
-    float u[16], w[16];
-    tmem_ld16(tcol(2 * q), u);
-    tmem_ld16(tcol(2 * q + 1), w);
     float2 z[E];
+    {
+      float u[16], w[16];
+      if (q == 0) {  // s00 and the odd columns of (s22, s11)
+        tmem_ld16(tcol(0), u);
 #pragma unroll
-    for (int r = 0; r < E; ++r) z[r] = make_float2(u[r], w[r]);
+        for (int r = 0; r < E; ++r) z[r].x = u[r];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(tcol(2) + 16 * h, w);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) z[8 * h + i].y = w[2 * i + 1];
+        }
+      } else if (q == 1) {  // the even columns of (s22, s11) and the odd ones of (s02, s01)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(tcol(2) + 16 * h, u);
+          tmem_ld16(tcol(4) + 16 * h, w);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) z[8 * h + i] = make_float2(u[2 * i], w[2 * i + 1]);
+        }
+      } else {  // the even columns of (s02, s01) and s12
+        tmem_ld16(tcol(1), u);
+#pragma unroll
+        for (int r = 0; r < E; ++r) z[r].y = u[r];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(tcol(4) + 16 * h, w);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) z[8 * h + i].x = w[2 * i];
+        }
+      }
+    }
     fft_pencil<float, N, E, -1, Lay, Sync>(z, j, L, tw, Sync());
 #pragma unroll
     for (int r = 0; r < E; ++r) zo[L.idx(j + r * P)] = z[r];
@@ -999,6 +1043,122 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
       f2[k] = make_float2(0.5f * (zk.y - zm.y), -0.5f * (zk.x - zm.x));
     }
     Sync()();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(*tslot, CF::NCOLS);
+}
+
+// P1 with its Phi~ tile and cell indices in tensor memory (autotuner variant bit 16; FP32, radix 16, 16 columns
+// per CTA, N = 256).  k_p1 keeps each thread's 16 Phi~ values and cells in registers for all the terms of a launch
+// (125 registers: two CTAs of 8 warps per SM, latency-bound).  Here they sit in the thread's TMEM lane (columns
+// 0-31: Phi~ as (re, im) pairs, 32-47: cells; warps w and w + 4 share a lane quarter, the latter at column 64) and
+// are read back for every transform; with a single exchange buffer (a two-stage transform needs no second one)
+// three CTAs share an SM.  Same arithmetic as k_p1.
+template <int N>
+struct P1TCfg {
+  static constexpr int H = N / 2, E = 16, P = N / E, TC = 16, THREADS = TC * P;
+  static_assert(THREADS == 256, "two warps per TMEM lane quarter");
+  using Lay = ColLayout<float, N, TC, E, true>;
+  static constexpr uint32_t NCOLS = 128;
+  static size_t smem(int nb, int nm1) {
+    return (size_t)Lay::SIZE * 8 + (size_t)N * 8 + (size_t)N * 4 + (size_t)nb * nm1 * 4 + 16;
+  }
+};
+
+template <int N>
+__global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* __restrict__ phi, float2* __restrict__ Ta,
+                                                                  float2* __restrict__ Tb, const int16_t* __restrict__ lut,
+                                                                  const float* __restrict__ phitab, int nm1, int alpha0,
+                                                                  int nb, const float2* __restrict__ tw) {
+  using CF = P1TCfg<N>;
+  constexpr int E = CF::E, P = CF::P, TC = CF::TC, H = CF::H, NH = H + 1;
+  using Lay = typename CF::Lay;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm_nyq = reinterpret_cast<float2*>(smraw) + Lay::SIZE;  // N values (column 0 only)
+  int* sm_cn = reinterpret_cast<int*>(sm_nyq + N);                // N cells
+  float* sm_tab = reinterpret_cast<float*>(sm_cn + N);            // nb * nm1
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm_tab + nb * nm1);
+  const int c = threadIdx.x % TC, j = threadIdx.x / TC;
+  const Lay L{reinterpret_cast<float2*>(smraw), c};
+  const int cc = blockIdx.x * TC + c;
+  const int k1 = blockIdx.y;
+  const int b = blockIdx.z;
+  const int n1 = wrapn(k1, N);
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tmem_alloc(tslot, CF::NCOLS);
+  for (int i = threadIdx.x; i < nb * nm1; i += blockDim.x) sm_tab[i] = phitab[(long)alpha0 * nm1 + i];
+  const float2* pb = phi + ((long)b * N * N + k1) * NH;  // + k0 * N * NH + k2
+  if (blockIdx.x == 0) {
+    for (int k0 = threadIdx.x; k0 < N; k0 += blockDim.x) {
+      const int n0 = wrapn(k0, N);
+      sm_nyq[k0] = pb[(long)k0 * N * NH + H];
+      sm_cn[k0] = lut[n0 * n0 + n1 * n1 + H * H];
+    }
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tbase = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  {
+    float u[16];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k0 = j + (8 * h + i) * P;
+        const float2 v = pb[(long)k0 * N * NH + cc];
+        u[2 * i] = v.x;
+        u[2 * i + 1] = v.y;
+      }
+      tmem_st16(tbase + 16 * h, u);
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int n0 = wrapn(j + r * P, N);
+      u[r] = __int_as_float((int)lut[n0 * n0 + n1 * n1 + cc * cc]);
+    }
+    tmem_st16(tbase + 32, u);
+    tmem_wait_st();
+  }
+  const long fstride = (long)N * N * H;  // one field
+  const float fj = (float)j;
+  for (int a = 0; a < nb; ++a) {
+    const float* tab = sm_tab + a * nm1;
+#pragma unroll 1
+    for (int D = 0; D < 2; ++D) {
+      float2 v[E];
+      {
+        float cl[16], u[16];
+        tmem_ld16(tbase + 32, cl);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(tbase + 16 * h, u);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = 8 * h + i;
+            const float f = tab[__float_as_int(cl[r])];
+            float2 x = make_float2(f * u[2 * i], f * u[2 * i + 1]);
+            if (cc == 0) {
+              const int k0 = j + r * P;
+              const float fn = tab[sm_cn[k0]];
+              const float2 yn = sm_nyq[k0];
+              x = make_float2(x.x - fn * yn.y, x.y + fn * yn.x);
+            }
+            if (D) {  // n^D(k0), k0 = j + r P: k0 < N/2 exactly when r < E/2 (Nyquist: r = E/2, j = 0)
+              const float nd = r < E / 2 ? fj + (float)(r * P) : ((r == E / 2 && j == 0) ? 0.f : fj + (float)(r * P - N));
+              x = make_float2(-nd * x.y, nd * x.x);
+            }
+            v[r] = x;
+          }
+        }
+      }
+      fft_pencil<float, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
+      float2* dst = (D ? Tb : Ta) + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
+#pragma unroll
+      for (int r = 0; r < E; ++r) dst[(long)(j + r * P) * N * H] = v[r];
+    }
   }
   tmem_fence_before_sync();
   __syncthreads();

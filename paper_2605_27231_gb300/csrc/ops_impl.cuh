@@ -79,10 +79,25 @@ struct OpsT {
     return cudaGetLastError();
   }
   template <int N>
+  static cudaError_t p1_tm_v(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
+                             int alpha0, int nb, int batch, const void* tw, cudaStream_t st) {
+    using CF = P1TCfg<N>;
+    const size_t sm = CF::smem(nb, nm1);
+    auto k = k_p1_tm<N>;
+    SIGW_CHECK_LAUNCH(allow_smem(k, 227 * 1024));
+    dim3 grid((N / 2) / CF::TC, N, batch);
+    k<<<grid, CF::THREADS, sm, st>>>((const float2*)phi, (float2*)Ta, (float2*)Tb, lut, (const float*)phitab, nm1,
+                                     alpha0, nb, (const float2*)tw);
+    return cudaGetLastError();
+  }
+  template <int N>
   static cudaError_t p1_n(const void* phi, void* Ta, void* Tb, const int16_t* lut, const void* phitab, int nm1,
                           int alpha0, int nb, int batch, const void* tw, int variant, cudaStream_t st) {
     using SH = Shape<T, N>;
     using AL = AltStrided<T, N>;
+    if constexpr (sizeof(T) == 4 && N == 256) {  // Phi~ tile and cells in tensor memory
+      if (variant & 16) return p1_tm_v<N>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
+    }
     if constexpr (AL::exists) {
       if (variant & 1)
         return p1_v<N, AL::E, AL::TC>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);

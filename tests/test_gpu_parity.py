@@ -403,14 +403,15 @@ def test_graph_replay_equals_direct_launches(lib):
 @pytest.mark.parametrize("N", [128, 256])
 def test_every_variant_matches_oracle(lib, dec, N):
     """Each radix variant (bits 1, 2, 4 and all together; at 256^3 also the last pass with its accumulators in tensor
-    memory, bit 8) on sampled shells of a local-map field, vs the oracle."""
+    memory, bit 8, and the first pass with its tile in tensor memory, bit 16) on sampled shells of a local-map field,
+    vs the oracle."""
     spec = workloads.scaled(workloads.workload("local128"), N)
     shells = [3, N // 4]
     d10 = odec.build(n_alpha=10)
     ref, _, _ = _oracle(spec, d10, shells)
     with lib.Plan(N, spec.L, precision=32, n_alpha=10) as p:
         p.generate_spec(spec)
-        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)) + (((10, 8), (4, 15)) if N == 256 else ()):
+        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)) + (((10, 8), (4, 15), (10, 16), (8, 26)) if N == 256 else ()):
             p.set_tuning(B, v)
             np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
         with pytest.raises(lib.SigwError):
