@@ -145,7 +145,12 @@ def run_ours(args):
         plan.spectrum_async(dev_out.data_ptr())
 
     plan.generate_spec(spec, seeds=seeds)
-    tuned = dict(zip(("alpha_batch", "variant_bits", "tune_ms"), plan.autotune()))
+    if args.tuning:  # a fixed choice (terms per launch, variant bits) instead of the autotuner's
+        tb, tv = (int(x) for x in args.tuning.split(","))
+        plan.set_tuning(tb, tv)
+        tuned = {"alpha_batch": tb, "variant_bits": tv, "fixed": True}
+    else:
+        tuned = dict(zip(("alpha_batch", "variant_bits", "tune_ms"), plan.autotune()))
 
     for _ in range(args.warmup):
         step()
@@ -563,6 +568,7 @@ def main():
     ap.add_argument("--cpu-terms", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paper-scan", action="store_true")
+    ap.add_argument("--tuning", default="", help="B,V: terms per launch and variant bits instead of the autotuner")
     ap.add_argument("--alpha-batch", type=int, default=0,
                     help="separable terms per strided-pass launch (0: chosen by the autotuner)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64],
