@@ -42,13 +42,13 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 METRIC = "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp64_path; serving p50/p99 under serving)"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu capture per kernel kind at 256^3 FP32,
-# with the algorithmic bytes of the captured launch (the committed ncu summaries of k_p1, k_p2, k_p3 at 256^3).  These kernels move bytes in
+# with the algorithmic bytes of the captured launch (the committed ncu summaries of k_p1_tm, k_p2, k_p3_tm at 256^3).  These move bytes in
 # proportion to the term-realisations of a launch, so the traffic of a bench launch is the algorithmic bytes of
 # that launch times the captured ratio.  Valid only while the kernel source is unchanged since the capture.
 NCU_TRAFFIC_256 = {
-    "p1_inv_axis0_filter": (0.068546e9 + 1.281282e9, 0.0676e9 + 20 * 67.108864e6),
+    "p1_inv_axis0_filter": (0.0679936e9 + 1.281478e9, 0.0676e9 + 20 * 67.108864e6),  # k_p1_tm (tile in TMEM)
     "p2_inv_axis1": (1.073817e9 + 1.553402e9, 40 * 67.108864e6),
-    "p3_inv_axis2_product_fwd_axis2": (2.013373e9 + 0.026424e9, 30 * 67.108864e6 + 6 * 65536 * 2 * 8),
+    "p3_inv_axis2_product_fwd_axis2": (2.013356e9 + 0.0092119e9, 30 * 67.108864e6 + 6 * 65536 * 2 * 8),  # k_p3_tm
 }
 
 
