@@ -241,11 +241,11 @@ sigw_status sigw_server_destroy(sigw_server srv);
  * n_alpha; exactly opts->alpha_batch when that is set) and, where two exist (FP32, N >= 128), both radix
  * variants of the strided passes.  Keeps the fastest in the plan and in a process-wide table keyed by
  * (N, precision, max_batch, n_alpha) from which later plans with alpha_batch = 0 start; then times both radix
- * forms of the last inverse pass (FP32, N = 128, 256, 512) on the terms just produced; at FP32 256^3 it also times
- * the first pass with its Phi~ tile and cells in tensor memory and the radix-16 last pass with its accumulators in
- * tensor memory.  An untuned FP32 plan starts from the bits these runs chose on GB300 (2 from N = 128, 26 at
- * N = 256, 7 at N = 512).  Outputs nullable: chosen terms per launch, variant bits (1: alternative radix of the
- * first strided pass, 2: radix-16 last pass, 4: alternative radix of the second strided pass, 8: radix-16 last
+ * forms of the last inverse pass (FP32, N = 128, 256, 512) on the terms just produced; at FP32 N = 128, 256, 512 it
+ * also times the first pass with its Phi~ tile and cells in tensor memory and the radix-16 last pass with its
+ * accumulators in tensor memory.  An untuned FP32 plan starts from the bits measured fastest on GB300 (26 at
+ * N = 128 and 256, 15 at N = 512).  Outputs nullable: chosen terms per launch, variant bits (1: alternative radix of
+ * the first strided pass, 2: radix-16 last pass, 4: alternative radix of the second strided pass, 8: radix-16 last
  * pass with its accumulators in tensor memory, 16: first pass with its tile in tensor memory) and the time in ms of the
  * chosen strided passes plus last pass for one kernel (m = s).  Waits for the stream.
  * Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */

@@ -430,10 +430,10 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
   p->L = L;
   p->opts = o;
   p->B = auto_alpha_batch(o);
-  // Untuned default: the choices the autotuner made on GB300 at usr256 and broad512 (radix-16 last pass from
-  // 128^3; at 256^3 the first and last passes with their per-thread state in tensor memory; at 512^3 the
-  // 512-specific strided passes).  sigw_plan_autotune or the table may override it.
-  p->variant = o.precision == 32 ? (N == 512 ? 7 : (N == 256 ? 26 : (N >= 128 ? 2 : 0))) : 0;
+  // Untuned default: the choices measured fastest on GB300 (at 128^3 and 256^3 the first and the radix-16 last pass
+  // with their per-thread state in tensor memory; at 512^3 the 512-specific strided passes and the tensor-memory
+  // last pass).  sigw_plan_autotune or the table may override it.
+  p->variant = o.precision == 32 ? (N == 512 ? 15 : (N >= 128 ? 26 : 0)) : 0;
   std::string e;
   if (!sigw::build_decomposition(params_of(o), &p->dec, &e)) {
     delete p;
@@ -1054,7 +1054,7 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
     return SIGW_OK;
   };
   // first-pass candidates: the two radix forms and, where it exists, the radix-16 form with its tile in TMEM
-  const bool p1tm = p->opts.precision == 32 && N == 256;
+  const bool p1tm = p->opts.precision == 32 && (N == 128 || N == 256 || N == 512);
   const int p1bits[3] = {0, 1, 16};
   const int np1 = nvar + (p1tm ? 1 : 0);
   for (int B : cands) {

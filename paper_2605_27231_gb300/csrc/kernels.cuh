@@ -842,17 +842,17 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// P3 with its accumulators in tensor memory (autotuner variant bit 8; FP32, radix 16, N = 256).  The last pass
+// P3 with its accumulators in tensor memory (autotuner variant bit 8; FP32, radix 16, N = 128, 256, 512).  The last pass
 // above keeps the six product components of its 16 points per thread in registers (96 of its 254), which holds
 // it to one CTA of 8 warps per SM.  Here they live in TMEM, in the thread's lane: s00 in columns 0-15, s12 in
 // 16-31, (s22, s11) interleaved in 32-63 and (s02, s01) interleaved in 64-95, so a thread needs ~170 registers and
-// three CTAs of 8 rows (4 warps) share an SM.  One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the
+// three CTAs of 128 threads (4 warps; 16, 8 or 4 rows) share an SM.  One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the
 // stage is refilled for the next pair while the transforms run, and the other CTAs of the SM cover the copy.
 // Bounded waits, error flag and the drain before exit as in k_p3.
 template <int N>
 struct P3TCfg {
-  static constexpr int H = N / 2, E = 16, P = N / E, RPC = 8, THREADS = RPC * P;
-  static_assert(THREADS == 128, "one warp per TMEM lane quarter");
+  static constexpr int H = N / 2, E = 16, P = N / E, RPC = 128 / P, THREADS = RPC * P;  // 16 / 8 / 4 rows at N = 128 / 256 / 512
+  static_assert(THREADS == 128 && P <= 32, "one warp per TMEM lane quarter; a row inside one warp");
   using Lay = RowLayout<float, N, true, 4>;
   static constexpr int STAGE_ELEMS = 6 * RPC * H;  // three fields of two terms
   static constexpr uint32_t NCOLS = 128;           // TMEM columns per CTA (96 used)
@@ -1050,15 +1050,15 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
   if (warp == 0) tmem_dealloc(*tslot, CF::NCOLS);
 }
 
-// P1 with its Phi~ tile and cell indices in tensor memory (autotuner variant bit 16; FP32, radix 16, 16 columns
-// per CTA, N = 256).  k_p1 keeps each thread's 16 Phi~ values and cells in registers for all the terms of a launch
+// P1 with its Phi~ tile and cell indices in tensor memory (autotuner variant bit 16; FP32, radix 16, 256 threads
+// per CTA: 32, 16 or 8 columns at N = 128, 256, 512).  k_p1 keeps each thread's 16 Phi~ values and cells in registers for all the terms of a launch
 // (125 registers: two CTAs of 8 warps per SM, latency-bound).  Here they sit in the thread's TMEM lane (columns
 // 0-31: Phi~ as (re, im) pairs, 32-47: cells; warps w and w + 4 share a lane quarter, the latter at column 64) and
-// are read back for every transform; with a single exchange buffer (a two-stage transform needs no second one)
-// three CTAs share an SM.  Same arithmetic as k_p1.
+// are read back for every transform; with a single exchange buffer (free for a two-stage transform; a three-stage
+// one syncs between a stage's reads and writes) four CTAs share an SM.  Same arithmetic as k_p1.
 template <int N>
 struct P1TCfg {
-  static constexpr int H = N / 2, E = 16, P = N / E, TC = 16, THREADS = TC * P;
+  static constexpr int H = N / 2, E = 16, P = N / E, TC = 256 / P, THREADS = TC * P;  // 32 / 16 / 8 columns
   static_assert(THREADS == 256, "two warps per TMEM lane quarter");
   using Lay = ColLayout<float, N, TC, E, true>;
   static constexpr uint32_t NCOLS = 128;

@@ -57,7 +57,7 @@ struct OpsRT {
   // err: device int, OR-ed with 1 when a bounded wait of the bulk-copy pipeline gives up; wait_limit: clock
   // cycles after which a wait of the main loop gives up (kDefaultWaitLimit unless a test shrinks it).
   // variant bit 2 selects the radix-16 form where p3_variants(N) >= 2; bit 8 the radix-16 form with its
-  // accumulators in tensor memory where p3_variants(N) == 3 (FP32, N = 256).
+  // accumulators in tensor memory where p3_variants(N) == 3 (FP32, N = 128, 256, 512).
   static int p3_variants(int N);
   static cudaError_t p3(int N, const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
                         const void* tw, int* err, long long wait_limit, int variant, cudaStream_t st);

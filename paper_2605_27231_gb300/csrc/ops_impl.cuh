@@ -95,7 +95,7 @@ struct OpsT {
                           int alpha0, int nb, int batch, const void* tw, int variant, cudaStream_t st) {
     using SH = Shape<T, N>;
     using AL = AltStrided<T, N>;
-    if constexpr (sizeof(T) == 4 && N == 256) {  // Phi~ tile and cells in tensor memory
+    if constexpr (sizeof(T) == 4 && (N == 128 || N == 256 || N == 512)) {  // Phi~ tile and cells in tensor memory
       if (variant & 16) return p1_tm_v<N>(phi, Ta, Tb, lut, phitab, nm1, alpha0, nb, batch, tw, st);
     }
     if constexpr (AL::exists) {
@@ -149,7 +149,7 @@ struct OpsT {
   template <int N>
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
                           int* err, long long wait_limit, int variant, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4 && N == 256) {  // accumulators in tensor memory
+    if constexpr (sizeof(T) == 4 && (N == 128 || N == 256 || N == 512)) {  // accumulators in tensor memory
       if (variant & 8) return p3_tm_v<N>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
     }
     if constexpr (AltP3<T, N>::exists) {
@@ -288,9 +288,9 @@ int OpsRT<T>::rows_blocks(int N) {
 }
 template <typename T>
 int OpsRT<T>::p3_variants(int N) {
-  if (N == 128) return AltP3<T, 128>::exists ? 2 : 1;
-  if (N == 256) return AltP3<T, 256>::exists ? (sizeof(T) == 4 ? 3 : 2) : 1;
-  if (N == 512) return AltP3<T, 512>::exists ? 2 : 1;
+  if (N == 128) return AltP3<T, 128>::exists ? 3 : 1;  // FP32: radix 8, radix 16, radix 16 with TMEM accumulators
+  if (N == 256) return AltP3<T, 256>::exists ? 3 : 1;
+  if (N == 512) return AltP3<T, 512>::exists ? 3 : 1;
   return 1;
 }
 template <typename T>

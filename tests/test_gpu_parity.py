@@ -379,7 +379,7 @@ def test_broad512_small_shells_fp32_fp64(lib, dec):
     # every radix variant of the FP32 passes at this size (radix 32 strided passes, radix 16 last pass)
     with lib.Plan(spec.N, spec.L, precision=32) as p:
         p.generate_spec(spec)
-        for v in (1, 2, 4, 7):
+        for v in (1, 2, 4, 7, 15, 31):
             p.set_tuning(10, v)
             np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
 
@@ -403,15 +403,16 @@ def test_graph_replay_equals_direct_launches(lib):
 @pytest.mark.parametrize("N", [128, 256])
 def test_every_variant_matches_oracle(lib, dec, N):
     """Each radix variant (bits 1, 2, 4 and all together; at 256^3 also the last pass with its accumulators in tensor
-    memory, bit 8, and the first pass with its tile in tensor memory, bit 16) on sampled shells of a local-map field,
-    vs the oracle."""
+    memory, bit 8, and the first pass with its tile in tensor memory, bit 16; both also at 128^3) on sampled shells of
+    a local-map field, vs the oracle."""
     spec = workloads.scaled(workloads.workload("local128"), N)
     shells = [3, N // 4]
     d10 = odec.build(n_alpha=10)
     ref, _, _ = _oracle(spec, d10, shells)
     with lib.Plan(N, spec.L, precision=32, n_alpha=10) as p:
         p.generate_spec(spec)
-        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)) + (((10, 8), (4, 15), (10, 16), (8, 26)) if N == 256 else ()):
+        extra = {256: ((10, 8), (4, 15), (10, 16), (8, 26)), 128: ((10, 8), (5, 13), (10, 26))}[N]
+        for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)) + extra:
             p.set_tuning(B, v)
             np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
         with pytest.raises(lib.SigwError):
@@ -428,7 +429,7 @@ def test_autotune_keeps_results_and_seeds_later_plans(lib, dec):
         before = p.spectrum(shells)["omega"][0]
         B, v, ms = p.autotune()
         after = p.spectrum(shells)["omega"][0]
-    assert B in (4, 5, 8, 10, 16) and 0 <= v < 8 and ms > 0
+    assert B in (4, 5, 8, 10, 16) and 0 <= v < 32 and ms > 0
     np.testing.assert_allclose(after, before, rtol=2e-5)
     ref, _, _ = _oracle(spec, dec, shells)
     np.testing.assert_allclose(after, ref["omega"], rtol=1e-4)
