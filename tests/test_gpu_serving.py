@@ -109,3 +109,31 @@ def test_express_slot_serves_small_requests_beside_a_large_batch(lib):
     np.testing.assert_allclose(om_big, _alone(lib, big), rtol=1e-4)
     for s, (om, lat) in zip(small, res_small):
         np.testing.assert_allclose(om, _alone(lib, s), rtol=1e-4)
+
+
+def test_queue_head_is_not_starved_by_small_requests(lib):
+    """A 64^3 request whose plan fits the budget only after an idle 32^3 plan is evicted, queued ahead of a stream of
+    32^3 requests that an express slot could serve: while it cannot be admitted, no later request starts, so it
+    completes before the small stream does (instead of after it), and every result equals its single-plan value."""
+    import time
+    fp32 = lib.footprint(32, lib.default_opts(max_batch=2))
+    fp64 = lib.footprint(64, lib.default_opts(max_batch=2))
+    first = [_spec(32, "gauss", 400 + i) for i in range(2)]
+    big = _spec(64, "local", 410, F=1.5)
+    stream = [_spec(32, "usr", 420 + i, sigma=0.4) for i in range(24)]
+    with lib.Server(fp64 + 0.5 * fp32, max_slots=1, max_batch=2, precision=32) as srv:
+        srv.set_express(1, 32)
+        tf = [(time.perf_counter(), srv.submit(s)) for s in first]
+        tb = (time.perf_counter(), srv.submit(big))
+        ts = [(time.perf_counter(), srv.submit(s)) for s in stream]
+        res_first = [srv.wait(t, timeout_s=300) for _, t in tf]
+        om_big, lat_big = srv.wait(tb[1], timeout_s=300)
+        res_stream = [srv.wait(t, timeout_s=300) for _, t in ts]
+        st = srv.stats()
+    assert st["completed"] == 27 and st["failed"] == 0 and st["plans_evicted"] >= 1
+    big_done = tb[0] + lat_big
+    last_small_done = max(t0 + lat for (t0, _), (_, lat) in zip(ts, res_stream))
+    assert big_done < last_small_done
+    np.testing.assert_allclose(om_big, _alone(lib, big), rtol=1e-4)
+    for s, (om, _) in zip(first + stream, res_first + res_stream):
+        np.testing.assert_allclose(om, _alone(lib, s), rtol=1e-4)
