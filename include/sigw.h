@@ -246,8 +246,7 @@ sigw_status sigw_server_destroy(sigw_server srv);
  * accumulators in tensor memory.  An untuned FP32 plan starts from the bits measured fastest on GB300 (26 at
  * N = 128 and 256, 15 at N = 512).  Outputs nullable: chosen terms per launch, variant bits (1: alternative radix of
  * the first strided pass, 2: radix-16 last pass, 4: alternative radix of the second strided pass, 8: radix-16 last
- * pass with its accumulators in tensor memory, 16: first pass with its tile in tensor memory, 32: first and second
- * passes fused in one cluster kernel, FP32 256^3, with the last pass reading its swizzled tiles) and the time in ms of the
+ * pass with its accumulators in tensor memory, 16: first pass with its tile in tensor memory) and the time in ms of the
  * chosen strided passes plus last pass for one kernel (m = s).  Waits for the stream.
  * Errors: SIGW_ESTATE (no field), SIGW_EINVAL, SIGW_ECUDA. */
 sigw_status sigw_plan_autotune(sigw_plan plan, int n_c, int* out_alpha_batch, int* out_variant, double* out_ms);
@@ -259,9 +258,8 @@ sigw_status sigw_plan_set_tuning(sigw_plan plan, int alpha_batch, int variant);
 
 /* Per-kernel accounting of a plan.  Kernel kinds: 0 synthesis chain, 1 first inverse pass (filter,
  * gradient), 2 second inverse pass, 3 last inverse pass + product + first forward pass, 4 second forward
- * pass, 5 last forward pass + TT projection + shell sum, 6 bin finalisation, 7 first and second inverse
- * passes fused (variant bit 32). */
-#define SIGW_NKINDS 8
+ * pass, 5 last forward pass + TT projection + shell sum, 6 bin finalisation. */
+#define SIGW_NKINDS 7
 typedef struct sigw_profile {
   double ms[SIGW_NKINDS];        /* summed CUDA-event durations (only while event timing is on) */
   double bytes[SIGW_NKINDS];     /* algorithmic bytes: each input element read once, each output written once */

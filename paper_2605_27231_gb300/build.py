@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsigw.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["ops_f32.cu", "ops_f64.cu", "fused.cu", "api.cu", "serve.cu", "noalloc.cu"]
+CU_SOURCES = ["ops_f32.cu", "ops_f64.cu", "api.cu", "serve.cu", "noalloc.cu"]
 CXX_SOURCES = ["plan.cpp"]
 
 

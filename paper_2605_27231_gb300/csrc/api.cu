@@ -60,10 +60,10 @@ std::map<TuneKey, std::pair<int, int>> g_tune;
 
 // Sizes (bytes) of every device buffer of a plan.
 struct Sizes {
-  size_t phi, phiT, T, W, synth, F, F2, partial, out, lut, tab, tw, amp, rows_sq;
+  size_t phi, T, W, synth, F, F2, partial, out, lut, tab, tw, amp, rows_sq;
   int maxblk;
   size_t total() const {
-    return phi + phiT + T + std::max(W, synth) + F + F2 + partial + out + lut + tab + tw + amp + rows_sq + 4096;
+    return phi + T + std::max(W, synth) + F + F2 + partial + out + lut + tab + tw + amp + rows_sq + 4096;
   }
 };
 
@@ -76,7 +76,6 @@ Sizes sizes_of(int N, const sigw_opts& o) {
   sigw::LaunchShape sh = o.precision == 64 ? sigw::OpsRT<double>::shape(N) : sigw::OpsRT<float>::shape(N);
   s.maxblk = sh.maxblk_f3;
   s.phi = mb * NN * NH * cel;
-  s.phiT = sigw::fused_supported(N, o.precision) ? s.phi : 0;  // k2-major copy for the fused first/second pass
   s.T = 2 * mb * (size_t)B * NN * H * cel;
   s.W = mb * 3 * (size_t)o.n_alpha * NN * H * cel;
   // the jackknife reuses W after each shell: two standard + two packed half spectra + two real fields
@@ -121,8 +120,6 @@ struct sigw_plan_s {
   // device buffers
   std::vector<void*> allocs;
   void* d_phi = nullptr;
-  void* d_phiT = nullptr;  // Phi~ in k2-major order (fused first/second pass only)
-  bool fused_ok = false;   // the fused first/second pass exists for this N and precision (variant bit 32)
   void* d_T = nullptr;     // first-pass output (two fields per term of an alpha batch)
   void* d_work = nullptr;  // W during the hot loop, synthesis scratch during sigw_generate / sigw_fft3d
   void* d_F = nullptr;
@@ -473,8 +470,6 @@ sigw_status sigw_plan_create(int N, double L, const sigw_opts* opts, void* cuda_
     ptr = reinterpret_cast<decltype(ptr)>(_q);              \
   } while (0)
   ALLOC(p->d_phi, p->sz.phi);
-  p->fused_ok = sigw::fused_supported(N, o.precision);
-  if (p->fused_ok) ALLOC(p->d_phiT, p->sz.phiT);
   ALLOC(p->d_T, p->sz.T);
   ALLOC(p->d_work, std::max(p->sz.W, p->sz.synth));
   ALLOC(p->d_F, p->sz.F);
@@ -674,8 +669,6 @@ sigw_status sigw_generate_batch(sigw_plan p, const sigw_pzeta* pz, const sigw_ng
     RUN(p, 0, Yb + Xb, "unpack (Phi)",
         OPS(p, unpack, N, Y, p->d_phi, batch, nullptr, 0L, (2.0 / 3.0) * dx * dx * dx, 1, st));
   }
-  if (p->fused_ok)
-    RUN(p, 0, 2.0 * Xb, "Phi~ to k2-major order", sigw::fused_phi_k2major(N, p->d_phi, p->d_phiT, batch, st));
   std::vector<unsigned long long> hits(batch, 0);
   if (any_usr) {
     CKP(p, cudaMemcpyAsync(hits.data(), p->d_hits, sizeof(unsigned long long) * batch, cudaMemcpyDeviceToHost, st),
@@ -739,19 +732,12 @@ static sigw_status enqueue_spectrum(sigw_plan p, const std::vector<int>& sh, con
     for (int n1 = n1lo; n1 < n1lo + nk1; ++n1)
       for (int n2 = 0; n2 <= n_c; ++n2) disk += (n1 * n1 + n2 * n2 <= n_c * n_c + n_c);
     for (int m = 0; m < 2; ++m) {
-      if (p->fused_ok && (var & 32)) {
-        // fused first/second pass: all terms in one launch; reads Phi~ once and writes three fields per term
-        RUN(p, 7, phib + 3.0 * n_alpha * fieldb, "P1+P2 fused",
-            sigw::fused_p12(N, p->d_phiT, p->d_work, lut, p->d_phitab[m], nm1, n_alpha, 0, n_alpha, batch, p->d_tw,
-                            p->d_err, p->wait_limit, st));
-      } else {
-        for (int a0 = 0; a0 < n_alpha; a0 += p->B) {
-          const int nb = std::min(p->B, n_alpha - a0);
-          RUN(p, 1, phib + 2.0 * nb * fieldb, "P1",
-              OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, var, st));
-          RUN(p, 2, 5.0 * nb * fieldb, "P2",
-              OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, var, st));
-        }
+      for (int a0 = 0; a0 < n_alpha; a0 += p->B) {
+        const int nb = std::min(p->B, n_alpha - a0);
+        RUN(p, 1, phib + 2.0 * nb * fieldb, "P1",
+            OPS(p, p1, N, p->d_phi, Ta, Tb, lut, p->d_phitab[m], nm1, a0, nb, batch, p->d_tw, var, st));
+        RUN(p, 2, 5.0 * nb * fieldb, "P2",
+            OPS(p, p2, N, Ta, Tb, p->d_work, n_alpha, a0, nb, batch, p->d_tw, var, st));
       }
       RUN(p, 3, 3.0 * n_alpha * fieldb + 6.0 * batch * NN * ncp * cel, "P3",
           OPS(p, p3, N, p->d_work, p->d_sigma[m], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err, p->wait_limit,
@@ -1130,32 +1116,11 @@ sigw_status sigw_plan_autotune(sigw_plan p, int n_c, int* out_alpha_batch, int* 
       best += t3[bv];
     }
   }
-  // the fused first/second pass with the last pass reading its swizzled tiles, against the best unfused choice
-  int fused = 0;
-  if (status == SIGW_OK && p->fused_ok) {
-    float tf = 1e30f;
-    for (int rep = 0; rep < 2 && status == SIGW_OK; ++rep) {
-      cudaEventRecord(e0, st);
-      cudaError_t e = sigw::fused_p12(N, p->d_phiT, p->d_work, lut, p->d_phitab[0], nm1, n_alpha, 0, n_alpha, batch,
-                                      p->d_tw, p->d_err, sigw::kDefaultWaitLimit, st);
-      if (e == cudaSuccess)
-        e = OPS(p, p3, N, p->d_work, p->d_sigma[0], n_alpha, p->d_F, n_c, batch, p->d_tw, p->d_err,
-                sigw::kDefaultWaitLimit, 32, st);
-      cudaEventRecord(e1, st);
-      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&tf, e0, e1) != cudaSuccess)
-        status = cuda_fail(p, e != cudaSuccess ? e : cudaGetLastError(), "autotune fused pass");
-    }
-    if (status == SIGW_OK && tf < best) {
-      best = tf;
-      fused = 32;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != SIGW_OK) return status;
   p->B = bestB;
-  p->variant = bestV | bestP3 | fused;
+  p->variant = bestV | bestP3;
   if (p->graph) {  // the captured loop used the old choice
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
@@ -1231,8 +1196,7 @@ sigw_status sigw_target_scan(sigw_plan p, const sigw_pzeta* pz, const sigw_ngmap
 
 sigw_status sigw_plan_set_tuning(sigw_plan p, int alpha_batch, int variant) {
   if (!p) return SIGW_EINVAL;
-  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 63 ||
-      ((variant & 32) && !p->fused_ok))
+  if (alpha_batch < 1 || alpha_batch > max_alpha_batch(p->opts) || variant < 0 || variant > 31)
     return fail(p, SIGW_EINVAL, "sigw_plan_set_tuning: alpha_batch or variant out of range");
   CKP(p, cudaSetDevice(p->dev), "cudaSetDevice");
   CKP(p, cudaStreamSynchronize(p->st), "set_tuning");

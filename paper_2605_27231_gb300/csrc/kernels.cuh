@@ -859,10 +859,7 @@ struct P3TCfg {
   static constexpr size_t SMEM = (size_t)STAGE_ELEMS * 8 + (size_t)RPC * Lay::SIZE * 8 + 16;
 };
 
-// SWZ (N = 256): W holds the swizzled 8-row tiles of the fused first/second pass; element (rr, c) of a tile sits at
-// 8 c + 2 ((rr / 2) xor ((c / 2) mod 4)) + rr mod 2.  For the columns a thread reads (c = j + 16 r, or 256 - 16 r - j
-// for the Hermitian partner) that is a per-thread base plus or minus 128 r, so the reads cost what plain rows do.
-template <int N, bool SWZ = false>
+template <int N>
 __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* __restrict__ W,
                                                                   const float* __restrict__ sigma, int n_alpha,
                                                                   float2* __restrict__ F, int n_c,
@@ -931,64 +928,18 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
     const float2* w21 = wb0 + 5 * RPC * H;
     // inputs of the three transforms: (g0^a + i g0^{a+1}), (g2^a + i g1^a), (g2^{a+1} + i g1^{a+1})
     float2 zB[E], za[E], zb[E];
-    if constexpr (SWZ) {
-      static_assert(N == 256 && E == 16 && P == 16 && RPC == 8, "swizzled tiles: 8 rows of 256^3");
-      const int jr = (16 - j) & 15;
-      const int bf = 8 * j + 2 * ((rr >> 1) ^ ((j >> 1) & 3)) + (rr & 1);
-      const int br = 2048 - 8 * j + 2 * ((rr >> 1) ^ ((jr >> 1) & 3)) + (rr & 1);
-      const float2* tile[6];
 #pragma unroll
-      for (int f = 0; f < 6; ++f) tile[f] = ring + f * RPC * H;
-      // the Hermitian value at k = j + r P (plain) and i n^D(k) times it (grad), as row_plain / row_grad
-      auto plain = [&](const float2* tl, int r) -> float2 {
-        if (r < E / 2) {
-          const float2 v = tl[bf + 128 * r];
-          return (r == 0 && j == 0) ? make_float2(v.x, 0.f) : v;
-        }
-        const bool hz = (r == E / 2) && (j == 0);
-        const float2 v = tl[hz ? bf : br - 128 * r];
-        return hz ? make_float2(v.y, 0.f) : make_float2(v.x, -v.y);
-      };
-      auto grad = [&](const float2* tl, int r) -> float2 {
-        if (r < E / 2) {
-          const float2 x = tl[bf + 128 * r];
-          const float n = fj + (float)(r * P);
-          return make_float2(-n * x.y, n * x.x);
-        }
-        const bool hz = (r == E / 2) && (j == 0);
-        const float2 v = tl[hz ? bf : br - 128 * r];
-        const float2 x = make_float2(v.x, -v.y);
-        const float n = hz ? 0.f : fj + (float)(r * P - N);
-        return make_float2(-n * x.y, n * x.x);
-      };
-#pragma unroll
-      for (int r = 0; r < E; ++r) {
-        const float2 g0 = plain(tile[2], r);
-        const float2 g0b = two ? plain(tile[5], r) : make_float2(0.f, 0.f);
-        zB[r] = make_float2(g0.x - g0b.y, g0.y + g0b.x);
-        const float2 g2 = grad(tile[0], r), g1 = plain(tile[1], r);
-        za[r] = make_float2(g2.x - g1.y, g2.y + g1.x);
-        if (two) {
-          const float2 h2 = grad(tile[3], r), h1 = plain(tile[4], r);
-          zb[r] = make_float2(h2.x - h1.y, h2.y + h1.x);
-        } else {
-          zb[r] = make_float2(0.f, 0.f);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < E; ++r) {
-        const float2 g0 = row_plain<float, N, E>(w20, j, r);
-        const float2 g0b = two ? row_plain<float, N, E>(w21, j, r) : make_float2(0.f, 0.f);
-        zB[r] = make_float2(g0.x - g0b.y, g0.y + g0b.x);
-        const float2 g2 = row_grad<float, N, E>(wb0, j, r, fj), g1 = row_plain<float, N, E>(w10, j, r);
-        za[r] = make_float2(g2.x - g1.y, g2.y + g1.x);
-        if (two) {
-          const float2 h2 = row_grad<float, N, E>(wb1, j, r, fj), h1 = row_plain<float, N, E>(w11, j, r);
-          zb[r] = make_float2(h2.x - h1.y, h2.y + h1.x);
-        } else {
-          zb[r] = make_float2(0.f, 0.f);
-        }
+    for (int r = 0; r < E; ++r) {
+      const float2 g0 = row_plain<float, N, E>(w20, j, r);
+      const float2 g0b = two ? row_plain<float, N, E>(w21, j, r) : make_float2(0.f, 0.f);
+      zB[r] = make_float2(g0.x - g0b.y, g0.y + g0b.x);
+      const float2 g2 = row_grad<float, N, E>(wb0, j, r, fj), g1 = row_plain<float, N, E>(w10, j, r);
+      za[r] = make_float2(g2.x - g1.y, g2.y + g1.x);
+      if (two) {
+        const float2 h2 = row_grad<float, N, E>(wb1, j, r, fj), h1 = row_plain<float, N, E>(w11, j, r);
+        zb[r] = make_float2(h2.x - h1.y, h2.y + h1.x);
+      } else {
+        zb[r] = make_float2(0.f, 0.f);
       }
     }
     __syncthreads();  // the stage has been read: refill it for the next pair while the transforms run

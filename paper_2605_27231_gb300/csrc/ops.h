@@ -71,15 +71,6 @@ struct OpsRT {
   static cudaError_t subvol(int N, int M, const void* R, int nfields, double* out, cudaStream_t st);
 };
 
-// Fused first and second inverse passes (fused.cu; FP32, N = 256; variant bit 32): Phi~ to k2-major order, and the
-// cluster kernel writing the three fields of terms alpha0 .. alpha0 + nb - 1 as swizzled 8-row tiles, which the last
-// pass reads with variant bit 32.  err / wait_limit as for the last pass.
-bool fused_supported(int N, int precision);
-cudaError_t fused_phi_k2major(int N, const void* X, void* XT, int batch, cudaStream_t st);
-cudaError_t fused_p12(int N, const void* phiT, void* W, const int16_t* lut, const void* phitab, int nm1, int n_alpha,
-                      int alpha0, int nb, int batch, const void* tw, int* err, long long wait_limit,
-                      cudaStream_t st);
-
 extern template struct OpsRT<float>;
 extern template struct OpsRT<double>;
 

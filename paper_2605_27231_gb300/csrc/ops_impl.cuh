@@ -135,11 +135,11 @@ struct OpsT {
                                            wait_limit);
     return cudaGetLastError();
   }
-  template <int N, bool SWZ = false>
+  template <int N>
   static cudaError_t p3_tm_v(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch,
                              const void* tw, int* err, long long wait_limit, cudaStream_t st) {
     using CF = P3TCfg<N>;
-    auto k = k_p3_tm<N, SWZ>;
+    auto k = k_p3_tm<N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, CF::SMEM));
     dim3 grid((N * N) / CF::RPC, batch);
     k<<<grid, CF::THREADS, CF::SMEM, st>>>((const float2*)W, (const float*)sigma, n_alpha, (float2*)F, n_c,
@@ -149,9 +149,6 @@ struct OpsT {
   template <int N>
   static cudaError_t p3_n(const void* W, const void* sigma, int n_alpha, void* F, int n_c, int batch, const void* tw,
                           int* err, long long wait_limit, int variant, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4 && N == 256) {  // the swizzled tiles of the fused first/second pass
-      if (variant & 32) return p3_tm_v<N, true>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
-    }
     if constexpr (sizeof(T) == 4 && (N == 128 || N == 256 || N == 512)) {  // accumulators in tensor memory
       if (variant & 8) return p3_tm_v<N>(W, sigma, n_alpha, F, n_c, batch, tw, err, wait_limit, st);
     }

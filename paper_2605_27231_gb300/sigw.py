@@ -46,9 +46,9 @@ def _spec_map(s):
     return _ngmap(s.kind, s.F_NL, s.G_NL, s.usr_floor, getattr(s, "alpha_NL", 0.0), getattr(s, "beta_NL", 0.0))
 
 
-NKINDS = 8
+NKINDS = 7
 KINDS = ("synth", "p1_inv_axis0_filter", "p2_inv_axis1", "p3_inv_axis2_product_fwd_axis2", "f2_fwd_axis1",
-         "f3_fwd_axis0_tt_bin", "bin_finalise", "p12_fused_inv_axes01")
+         "f3_fwd_axis0_tt_bin", "bin_finalise")
 
 
 class Profile(C.Structure):

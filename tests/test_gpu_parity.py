@@ -411,7 +411,7 @@ def test_every_variant_matches_oracle(lib, dec, N):
     ref, _, _ = _oracle(spec, d10, shells)
     with lib.Plan(N, spec.L, precision=32, n_alpha=10) as p:
         p.generate_spec(spec)
-        extra = {256: ((10, 8), (4, 15), (10, 16), (8, 26), (10, 56), (4, 40)), 128: ((10, 8), (5, 13), (10, 26))}[N]
+        extra = {256: ((10, 8), (4, 15), (10, 16), (8, 26)), 128: ((10, 8), (5, 13), (10, 26))}[N]
         for B, v in ((4, 0), (10, 1), (10, 2), (8, 4), (5, 7)) + extra:
             p.set_tuning(B, v)
             np.testing.assert_allclose(p.spectrum(shells)["omega"][0], ref["omega"], rtol=1e-4)
