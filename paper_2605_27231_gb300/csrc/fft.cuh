@@ -187,6 +187,21 @@ template <typename T, int N, bool ONE = false, int PADSH = 3> struct RowLayout {
   __device__ __forceinline__ int idx(int p) const { return p + (p >> PADSH); }
 };
 
+// RowLayoutV: one buffer per pencil with two pad elements after every 16, so the 16 consecutive outputs of a
+//   thread's first radix-16 stage form 16-byte aligned pairs (one 128-bit store per two values); unit-stride reads
+//   of 16 threads cover 128 contiguous bytes.  The pitch N + N/8 + 8 puts consecutive rows 64 bytes apart in the
+//   128-byte bank cycle, so two rows of 8 threads each also read conflict-free.
+template <typename T, int N> struct RowLayoutV {
+  static constexpr bool SINGLE = true;
+  static constexpr bool VEC = true;
+  static constexpr int BUF = N + N / 8 + 8;
+  static constexpr int SIZE = BUF;
+  static_assert(N % 16 == 0 && (BUF * (int)sizeof(cx<T>)) % 16 == 0, "16-byte aligned rows");
+  cx<T>* base;
+  __device__ __forceinline__ cx<T>* buf(int) const { return base; }
+  __device__ __forceinline__ int idx(int p) const { return p + 2 * (p >> 4); }
+};
+
 // ONE: a single buffer (a stage syncs between its reads and writes), for tiles whose two buffers would not
 // leave room for a second CTA per SM.
 template <typename T, int N, int TC, int E, bool ONE = false> struct ColLayout {

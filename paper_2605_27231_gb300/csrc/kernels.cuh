@@ -13,6 +13,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 
 #include "fft.cuh"
 #include "ops.h"
@@ -842,6 +843,70 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// Two-stage inverse pencil transform of N = 16 R points (R = 8, 16: N = 128, 256), radix 16 then radix R, with the
+// last stage's twiddles held in tensor memory.  Thread j of a pencil needs the same NB (R - 1) twiddles
+// W^{-r k}, k = (j + t P) mod 16 (t < NB = 16 / R, 0 < r < R), in every transform of a launch; tw_tm_store writes
+// them once into 32 columns of its lane (twiddle q = t (R - 1) + r - 1 in columns 2q, 2q + 1), and
+// fft_pencil_tw_tm reads them with two tensor-memory loads instead of NB (R - 1) table loads.  Its first stage
+// writes the exchange row as 16-byte pairs (RowLayoutV).  Same arithmetic, in the same order, as
+// fft_pencil<float, N, 16, +1>.
+template <int N> struct TwTm {
+  static constexpr int E = 16, P = N / E, R = N / E, NB = E / R;
+  static_assert(R >= 2 && R <= E && NB * (R - 1) <= 16, "two stages, at most 16 twiddles");
+};
+template <int N>
+__device__ __forceinline__ void tw_tm_store(uint32_t taddr, int j, const float2* __restrict__ tw) {
+  using C = TwTm<N>;
+  float w[2][16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) w[0][i] = w[1][i] = 0.f;
+#pragma unroll
+  for (int t = 0; t < C::NB; ++t) {
+    const int k = (j + t * C::P) & 15;
+#pragma unroll
+    for (int r = 1; r < C::R; ++r) {
+      const int q = t * (C::R - 1) + r - 1;
+      const float2 x = conjg<float>(__ldg(tw + r * k));  // stride N / (16 R) = 1
+      w[q >> 3][2 * (q & 7)] = x.x;
+      w[q >> 3][2 * (q & 7) + 1] = x.y;
+    }
+  }
+  tmem_st16(taddr, w[0]);
+  tmem_st16(taddr + 16, w[1]);
+}
+template <int N, typename Lay, typename Sync>
+__device__ __forceinline__ void fft_pencil_tw_tm(float2 (&v)[16], int j, const Lay& L, uint32_t tw_taddr, Sync sync) {
+  using C = TwTm<N>;
+  constexpr int E = C::E, P = C::P, R = C::R, NB = C::NB;
+  static_assert(Lay::VEC && Lay::SINGLE, "one exchange row with 16-byte pairs");
+  float2* x = L.buf(0);
+  dftR<float, +1, E>(v);
+#pragma unroll
+  for (int m = 0; m < E / 2; ++m)
+    *reinterpret_cast<float4*>(x + L.idx(j * E + 2 * m)) =
+        make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+  sync();
+  float w[2][16];
+  tmem_ld16(tw_taddr, w[0]);
+  tmem_ld16(tw_taddr + 16, w[1]);
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    const int jj = j + t * P;
+    float2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = x[L.idx(jj + r * (N / R))];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const int q = t * (R - 1) + r - 1;
+      a[r] = mul<float>(a[r], make_float2(w[q >> 3][2 * (q & 7)], w[q >> 3][2 * (q & 7) + 1]));
+    }
+    dftR<float, +1, R>(a);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[t + r * NB] = a[r];
+  }
+  sync();  // the row may be rewritten at once
+}
+
 // P3 with its accumulators in tensor memory (autotuner variant bit 8; FP32, radix 16, N = 128, 256, 512).  The last pass
 // above keeps the six product components of its 16 points per thread in registers (96 of its 254), which holds
 // it to one CTA of 8 warps per SM.  Here they live in TMEM, in the thread's lane: s00 in columns 0-15, s12 in
@@ -853,9 +918,11 @@ template <int N>
 struct P3TCfg {
   static constexpr int H = N / 2, E = 16, P = N / E, RPC = 128 / P, THREADS = RPC * P;  // 16 / 8 / 4 rows at N = 128 / 256 / 512
   static_assert(THREADS == 128 && P <= 32, "one warp per TMEM lane quarter; a row inside one warp");
-  using Lay = RowLayout<float, N, true, 4>;
+  // two-stage transforms (N <= 256): twiddles in TMEM columns 96-127 and 16-byte exchange stores
+  static constexpr bool TWTM = N <= 256;
+  using Lay = std::conditional_t<TWTM, RowLayoutV<float, N>, RowLayout<float, N, true, 4>>;
   static constexpr int STAGE_ELEMS = 6 * RPC * H;  // three fields of two terms
-  static constexpr uint32_t NCOLS = 128;           // TMEM columns per CTA (96 used)
+  static constexpr uint32_t NCOLS = 128;           // TMEM columns per CTA (96, or 128 with the twiddles)
   static constexpr size_t SMEM = (size_t)STAGE_ELEMS * 8 + (size_t)RPC * Lay::SIZE * 8 + 16;
 };
 
@@ -899,6 +966,7 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
     for (int i = 0; i < 16; ++i) z0[i] = 0.f;
 #pragma unroll
     for (int c = 0; c < 6; ++c) tmem_st16(tcol(c), z0);
+    if constexpr (CF::TWTM) tw_tm_store<N>(tcol(6), j, tw);
     tmem_wait_st();
   }
   auto issue = [&](int pr) {  // thread 0: the six row blocks of term pair pr into the stage
@@ -947,9 +1015,15 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
       issue(pr + 1);
       issued = pr + 2;
     }
-    fft_pencil<float, N, E, +1, Lay, Sync>(zB, j, L, tw, Sync());
-    fft_pencil<float, N, E, +1, Lay, Sync>(za, j, L, tw, Sync());
-    fft_pencil<float, N, E, +1, Lay, Sync>(zb, j, L, tw, Sync());
+    if constexpr (CF::TWTM) {
+      fft_pencil_tw_tm<N, Lay, Sync>(zB, j, L, tcol(6), Sync());
+      fft_pencil_tw_tm<N, Lay, Sync>(za, j, L, tcol(6), Sync());
+      fft_pencil_tw_tm<N, Lay, Sync>(zb, j, L, tcol(6), Sync());
+    } else {
+      fft_pencil<float, N, E, +1, Lay, Sync>(zB, j, L, tw, Sync());
+      fft_pencil<float, N, E, +1, Lay, Sync>(za, j, L, tw, Sync());
+      fft_pencil<float, N, E, +1, Lay, Sync>(zb, j, L, tw, Sync());
+    }
     const float sa = sigma[a], sb = two ? sigma[a + 1] : 0.f;
     // za = (g2a, g1a), zb = (g2b, g1b), zB = (g0a, g0b).  Chunks: s00 and s12 (16 columns each), (s22, s11) and
     // (s02, s01) interleaved (32 columns each), so the pair updates are paired (FP32x2) multiply-adds.
