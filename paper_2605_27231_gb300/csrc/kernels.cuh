@@ -1302,11 +1302,27 @@ __device__ __forceinline__ void tt_amp(int n0, int n1, int n2, const double2* S,
   ap = make_double2((uu.x - vv.x) * 0.70710678118654752440, (uu.y - vv.y) * 0.70710678118654752440);
   ax = make_double2(uv.x * 1.41421356237309504880, uv.y * 1.41421356237309504880);
 }
-// sum over the two polarisations of |e^l_ij(k_hat) S_ij|^2
+// Sum over the two polarisations of |e^l_ij(k_hat) S_ij|^2, written with the TT projector instead of the basis:
+// sum_l e^l_ij e^l_lm = (P_il P_jm + P_im P_jl - P_ij P_lm) / 2 with P = I - n n^T / |n|^2, which annihilates the
+// identity, so S may first lose its trace (S' = S - tr(S) I / 3; that also removes most of the cancellation when S
+// is near-isotropic).  For symmetric S':
+//   |S'|^2 - 2 |S' n|^2 / |n|^2 + |n.S'.n|^2 / (2 |n|^4),
+// rational in the integer mode (one division, no square root) and the same for n and -n.
 __device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2* S) {
-  double2 ap, ax;
-  tt_amp(n0, n1, n2, S, ap, ax);
-  return ap.x * ap.x + ap.y * ap.y + ax.x * ax.x + ax.y * ax.y;
+  const double m0 = n0, m1 = n1, m2 = n2;
+  const double inv = 1.0 / (m0 * m0 + m1 * m1 + m2 * m2);
+  const double tx = (S[0].x + S[1].x + S[2].x) * (1.0 / 3.0), ty = (S[0].y + S[1].y + S[2].y) * (1.0 / 3.0);
+  const double2 s00 = make_double2(S[0].x - tx, S[0].y - ty), s11 = make_double2(S[1].x - tx, S[1].y - ty),
+                s22 = make_double2(S[2].x - tx, S[2].y - ty), s01 = S[3], s02 = S[4], s12 = S[5];
+  const double2 a0 = make_double2(s00.x * m0 + s01.x * m1 + s02.x * m2, s00.y * m0 + s01.y * m1 + s02.y * m2);
+  const double2 a1 = make_double2(s01.x * m0 + s11.x * m1 + s12.x * m2, s01.y * m0 + s11.y * m1 + s12.y * m2);
+  const double2 a2 = make_double2(s02.x * m0 + s12.x * m1 + s22.x * m2, s02.y * m0 + s12.y * m1 + s22.y * m2);
+  const double qx = m0 * a0.x + m1 * a1.x + m2 * a2.x, qy = m0 * a0.y + m1 * a1.y + m2 * a2.y;
+  const double ss = s00.x * s00.x + s00.y * s00.y + s11.x * s11.x + s11.y * s11.y + s22.x * s22.x + s22.y * s22.y +
+                    2.0 * (s01.x * s01.x + s01.y * s01.y + s02.x * s02.x + s02.y * s02.y + s12.x * s12.x +
+                           s12.y * s12.y);
+  const double aa = a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y + a2.x * a2.x + a2.y * a2.y;
+  return ss - 2.0 * aa * inv + 0.5 * (qx * qx + qy * qy) * inv * inv;
 }
 
 // F3: forward DFT along axis 0 of the six components for a tile of columns (n1 fixed, n2 = k2),
@@ -1363,18 +1379,23 @@ __global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_
         double2 S[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) S[q] = make_double2((double)X[q][r].x, (double)X[q][r].y);
-        double2 ap, ax;
-        tt_amp(n0, n1, n2, S, ap, ax);
-        acc += ap.x * ap.x + ap.y * ap.y + ax.x * ax.x + ax.y * ax.y;
+        const double pw = tt_power(n0, n1, n2, S);
+        acc += pw;
         if (Xj) {
+          double2 ap, ax;
+          tt_amp(n0, n1, n2, S, ap, ax);
           constexpr long NNH = (long)N * N * (H + 1);
           const long o = ((long)b * 2 * N + (j + r * P)) * N * (H + 1) + (long)((n1 + N) % N) * (H + 1) + n2;
           Xj[o] = mk<T>((T)ap.x, (T)ap.y);
           Xj[o + NNH] = mk<T>((T)ax.y, (T)-ax.x);
         }
-        if (n2 > 0 && n2 < H) {
-          const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
-          acc += tt_power(p0, p1, -n2, S);
+        if (n2 > 0 && n2 < H) {  // the partner -n has the same projector unless n0 or n1 is a Nyquist index
+          if (n0 == H || n1 == H) {
+            const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
+            acc += tt_power(p0, p1, -n2, S);
+          } else {
+            acc += pw;
+          }
         }
       }
     }
