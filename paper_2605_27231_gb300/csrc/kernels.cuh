@@ -1333,7 +1333,7 @@ __device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2
 // Xj[b][0] = e^+ : S and Xj[b][1] = -i e^x : S (both Hermitian in this basis away from the Nyquist shell),
 // [b][f][k0][k1][k2], k2 = 0..N/2; every other entry is left as it is (zero).
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_f3(const cx<T>* __restrict__ F2, int n_c, int n1lo, int nk1,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_f3(const cx<T>* __restrict__ F2, int n_c, int n1lo, int nk1,
                                             double* __restrict__ partial, long pbstride,
                                             const cx<T>* __restrict__ tw, cx<T>* __restrict__ Xj) {
   using SH = Shape<T, N>;
