@@ -1127,15 +1127,17 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
 // P1 with its Phi~ tile and cell indices in tensor memory (autotuner variant bit 16; FP32, radix 16, 256 threads
 // per CTA: 32, 16 or 8 columns at N = 128, 256, 512).  k_p1 keeps each thread's 16 Phi~ values and cells in registers for all the terms of a launch
 // (125 registers: two CTAs of 8 warps per SM, latency-bound).  Here they sit in the thread's TMEM lane (columns
-// 0-31: Phi~ as (re, im) pairs, 32-47: cells; warps w and w + 4 share a lane quarter, the latter at column 64) and
-// are read back for every transform; with a single exchange buffer (free for a two-stage transform; a three-stage
+// 0-31: Phi~ as (re, im) pairs, 32-47: cells, 48-63 (N = 128): the current term's filter values, looked up once
+// for both fields; warps w and w + 4 share a lane quarter, the latter at column 64) and are read back for every transform;
+// with a single exchange buffer (free for a two-stage transform; a three-stage
 // one syncs between a stage's reads and writes) four CTAs share an SM.  Same arithmetic as k_p1.
 template <int N>
 struct P1TCfg {
   static constexpr int H = N / 2, E = 16, P = N / E, TC = 256 / P, THREADS = TC * P;  // 32 / 16 / 8 columns
   static_assert(THREADS == 256, "two warps per TMEM lane quarter");
   using Lay = ColLayout<float, N, TC, E, true>;
-  static constexpr uint32_t NCOLS = 128;
+  static constexpr bool FCACHE = N == 128;  // the term's filter values kept for the second field
+  static constexpr uint32_t NCOLS = 128;     // per warp group: Phi~ 0-31, cells 32-47, the term's filter 48-63
   static size_t smem(int nb, int nm1) {
     return (size_t)Lay::SIZE * 8 + (size_t)N * 8 + (size_t)N * 4 + (size_t)nb * nm1 * 4 + 16;
   }
@@ -1204,15 +1206,26 @@ __global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* _
     for (int D = 0; D < 2; ++D) {
       float2 v[E];
       {
-        float cl[16], u[16];
-        tmem_ld16(tbase + 32, cl);
+        // the filter values of this term: looked up from the cells for the first field and, at N = 128, kept in the
+        // lane's columns 48-63 for the second (the store completed during the first field's transform).  At 256 the
+        // pass is bound by its stores, and the extra tensor-memory traffic cost 1 %; it looks them up again.
+        float fl[16], u[16];
+        if (D == 0 || !CF::FCACHE) {
+          tmem_ld16(tbase + 32, fl);
+#pragma unroll
+          for (int r = 0; r < E; ++r) fl[r] = tab[__float_as_int(fl[r])];
+          if constexpr (CF::FCACHE) tmem_st16(tbase + 48, fl);
+        } else {
+          tmem_wait_st();
+          tmem_ld16(tbase + 48, fl);
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           tmem_ld16(tbase + 16 * h, u);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int r = 8 * h + i;
-            const float f = tab[__float_as_int(cl[r])];
+            const float f = fl[r];
             float2 x = make_float2(f * u[2 * i], f * u[2 * i + 1]);
             if (cc == 0) {
               const int k0 = j + r * P;
