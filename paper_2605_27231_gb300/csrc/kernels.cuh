@@ -1219,25 +1219,46 @@ __global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* _
           tmem_wait_st();
           tmem_ld16(tbase + 48, fl);
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tmem_ld16(tbase + 16 * h, u);
+        // the 8 inputs of half h.  DER: times i n0^D(k0), k0 = j + r P (k0 < N/2 exactly when r < E/2; zero on the
+        // Nyquist index r = E/2, j = 0), folded into the filter value.  NYQ: the CTA holds packed column 0, whose
+        // thread c = 0 adds i V(k2 = N/2) with its own cell.  Both are compile-time, so the other CTAs' loops carry
+        // no per-value branches.
+        auto fill = [&](auto der, auto nyq, int h) {
+          constexpr bool DER = decltype(der)::value, NYQ = decltype(nyq)::value;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int r = 8 * h + i;
-            const float f = fl[r];
-            float2 x = make_float2(f * u[2 * i], f * u[2 * i + 1]);
-            if (cc == 0) {
+            const float nd = r < E / 2 ? fj + (float)(r * P) : ((r == E / 2 && j == 0) ? 0.f : fj + (float)(r * P - N));
+            float2 x;
+            if (NYQ && cc == 0) {
+              const float f = fl[r];
+              x = make_float2(f * u[2 * i], f * u[2 * i + 1]);
               const int k0 = j + r * P;
               const float fn = tab[sm_cn[k0]];
               const float2 yn = sm_nyq[k0];
               x = make_float2(x.x - fn * yn.y, x.y + fn * yn.x);
-            }
-            if (D) {  // n^D(k0), k0 = j + r P: k0 < N/2 exactly when r < E/2 (Nyquist: r = E/2, j = 0)
-              const float nd = r < E / 2 ? fj + (float)(r * P) : ((r == E / 2 && j == 0) ? 0.f : fj + (float)(r * P - N));
-              x = make_float2(-nd * x.y, nd * x.x);
+              if constexpr (DER) x = make_float2(-nd * x.y, nd * x.x);
+            } else if constexpr (DER) {
+              const float g = fl[r] * nd;
+              x = make_float2(-g * u[2 * i + 1], g * u[2 * i]);
+            } else {
+              const float f = fl[r];
+              x = make_float2(f * u[2 * i], f * u[2 * i + 1]);
             }
             v[r] = x;
+          }
+        };
+        const std::true_type yes{};
+        const std::false_type no{};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(tbase + 16 * h, u);
+          if (blockIdx.x == 0) {
+            if (D) fill(yes, yes, h);
+            else fill(no, yes, h);
+          } else {
+            if (D) fill(yes, no, h);
+            else fill(no, no, h);
           }
         }
       }
