@@ -994,22 +994,28 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
     const float2* wb1 = wb0 + 3 * RPC * H;
     const float2* w11 = wb0 + 4 * RPC * H;
     const float2* w21 = wb0 + 5 * RPC * H;
-    // inputs of the three transforms: (g0^a + i g0^{a+1}), (g2^a + i g1^a), (g2^{a+1} + i g1^{a+1})
+    // inputs of the three transforms: (g0^a + i g0^{a+1}), (g2^a + i g1^a), (g2^{a+1} + i g1^{a+1}); whether the
+    // pair has a second term (all but an odd last pair) is chosen once, not per value
     float2 zB[E], za[E], zb[E];
+    auto assemble = [&](auto second) {
+      constexpr bool TWO = decltype(second)::value;
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const float2 g0 = row_plain<float, N, E>(w20, j, r);
-      const float2 g0b = two ? row_plain<float, N, E>(w21, j, r) : make_float2(0.f, 0.f);
-      zB[r] = make_float2(g0.x - g0b.y, g0.y + g0b.x);
-      const float2 g2 = row_grad<float, N, E>(wb0, j, r, fj), g1 = row_plain<float, N, E>(w10, j, r);
-      za[r] = make_float2(g2.x - g1.y, g2.y + g1.x);
-      if (two) {
-        const float2 h2 = row_grad<float, N, E>(wb1, j, r, fj), h1 = row_plain<float, N, E>(w11, j, r);
-        zb[r] = make_float2(h2.x - h1.y, h2.y + h1.x);
-      } else {
-        zb[r] = make_float2(0.f, 0.f);
+      for (int r = 0; r < E; ++r) {
+        const float2 g0 = row_plain<float, N, E>(w20, j, r);
+        const float2 g0b = TWO ? row_plain<float, N, E>(w21, j, r) : make_float2(0.f, 0.f);
+        zB[r] = make_float2(g0.x - g0b.y, g0.y + g0b.x);
+        const float2 g2 = row_grad<float, N, E>(wb0, j, r, fj), g1 = row_plain<float, N, E>(w10, j, r);
+        za[r] = make_float2(g2.x - g1.y, g2.y + g1.x);
+        if constexpr (TWO) {
+          const float2 h2 = row_grad<float, N, E>(wb1, j, r, fj), h1 = row_plain<float, N, E>(w11, j, r);
+          zb[r] = make_float2(h2.x - h1.y, h2.y + h1.x);
+        } else {
+          zb[r] = make_float2(0.f, 0.f);
+        }
       }
-    }
+    };
+    if (two) assemble(std::true_type{});
+    else assemble(std::false_type{});
     __syncthreads();  // the stage has been read: refill it for the next pair while the transforms run
     if (threadIdx.x == 0 && ok && pr + 1 < npairs) {
       issue(pr + 1);
@@ -1127,8 +1133,7 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
 // P1 with its Phi~ tile and cell indices in tensor memory (autotuner variant bit 16; FP32, radix 16, 256 threads
 // per CTA: 32, 16 or 8 columns at N = 128, 256, 512).  k_p1 keeps each thread's 16 Phi~ values and cells in registers for all the terms of a launch
 // (125 registers: two CTAs of 8 warps per SM, latency-bound).  Here they sit in the thread's TMEM lane (columns
-// 0-31: Phi~ as (re, im) pairs, 32-47: cells, 48-63 (N = 128): the current term's filter values, looked up once
-// for both fields; warps w and w + 4 share a lane quarter, the latter at column 64) and are read back for every transform;
+// 0-31: Phi~ as (re, im) pairs, 32-47: cells; warps w and w + 4 share a lane quarter, the latter at column 64) and are read back for every transform;
 // with a single exchange buffer (free for a two-stage transform; a three-stage
 // one syncs between a stage's reads and writes) four CTAs share an SM.  Same arithmetic as k_p1.
 template <int N>
@@ -1136,8 +1141,7 @@ struct P1TCfg {
   static constexpr int H = N / 2, E = 16, P = N / E, TC = 256 / P, THREADS = TC * P;  // 32 / 16 / 8 columns
   static_assert(THREADS == 256, "two warps per TMEM lane quarter");
   using Lay = ColLayout<float, N, TC, E, true>;
-  static constexpr bool FCACHE = N == 128;  // the term's filter values kept for the second field
-  static constexpr uint32_t NCOLS = 128;     // per warp group: Phi~ 0-31, cells 32-47, the term's filter 48-63
+  static constexpr uint32_t NCOLS = 128;  // per warp group: Phi~ 0-31, cells 32-47
   static size_t smem(int nb, int nm1) {
     return (size_t)Lay::SIZE * 8 + (size_t)N * 8 + (size_t)N * 4 + (size_t)nb * nm1 * 4 + 16;
   }
@@ -1206,19 +1210,12 @@ __global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* _
     for (int D = 0; D < 2; ++D) {
       float2 v[E];
       {
-        // the filter values of this term: looked up from the cells for the first field and, at N = 128, kept in the
-        // lane's columns 48-63 for the second (the store completed during the first field's transform).  At 256 the
-        // pass is bound by its stores, and the extra tensor-memory traffic cost 1 %; it looks them up again.
+        // the filter values of this term, looked up from the cells (keeping them in tensor memory for the second
+        // field was measured slower)
         float fl[16], u[16];
-        if (D == 0 || !CF::FCACHE) {
-          tmem_ld16(tbase + 32, fl);
+        tmem_ld16(tbase + 32, fl);
 #pragma unroll
-          for (int r = 0; r < E; ++r) fl[r] = tab[__float_as_int(fl[r])];
-          if constexpr (CF::FCACHE) tmem_st16(tbase + 48, fl);
-        } else {
-          tmem_wait_st();
-          tmem_ld16(tbase + 48, fl);
-        }
+        for (int r = 0; r < E; ++r) fl[r] = tab[__float_as_int(fl[r])];
         // the 8 inputs of half h.  DER: times i n0^D(k0), k0 = j + r P (k0 < N/2 exactly when r < E/2; zero on the
         // Nyquist index r = E/2, j = 0), folded into the filter value.  NYQ: the CTA holds packed column 0, whose
         // thread c = 0 adds i V(k2 = N/2) with its own cell.  Both are compile-time, so the other CTAs' loops carry
