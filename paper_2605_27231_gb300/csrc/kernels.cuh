@@ -906,6 +906,53 @@ __device__ __forceinline__ void fft_pencil_tw_tm(float2 (&v)[16], int j, const L
   }
   sync();  // the row may be rewritten at once
 }
+// As fft_pencil<float, N, 16, +1> for a two-stage transform, with the first 8 of the thread's last-stage twiddles
+// (q = t (R - 1) + r - 1 < 8, same order as TwTm) taken from 16 columns of its tensor-memory lane (written once by
+// tw8_tm_store) and the others from the table.  Any exchange layout.
+template <int N>
+__device__ __forceinline__ void tw8_tm_store(uint32_t taddr, int j, const float2* __restrict__ tw) {
+  using C = TwTm<N>;
+  float w[16];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = q / (C::R - 1), r = q % (C::R - 1) + 1;
+    const float2 x = conjg<float>(__ldg(tw + r * ((j + t * C::P) & 15)));
+    w[2 * q] = x.x;
+    w[2 * q + 1] = x.y;
+  }
+  tmem_st16(taddr, w);
+}
+template <int N, typename Lay, typename Sync>
+__device__ __forceinline__ void fft_pencil_tw8_tm(float2 (&v)[16], int j, const Lay& L, const float2* __restrict__ tw,
+                                                  uint32_t tw_taddr, Sync sync) {
+  using C = TwTm<N>;
+  constexpr int E = C::E, P = C::P, R = C::R, NB = C::NB;
+  float2* x = L.buf(0);
+  dftR<float, +1, E>(v);
+#pragma unroll
+  for (int r = 0; r < E; ++r) x[L.idx(j * E + r)] = v[r];
+  sync();
+  float w[16];
+  tmem_ld16(tw_taddr, w);
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    const int jj = j + t * P;
+    const int k = jj & 15;
+    float2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = x[L.idx(jj + r * (N / R))];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const int q = t * (R - 1) + r - 1;
+      const float2 wr = q < 8 ? make_float2(w[2 * q], w[2 * q + 1]) : twiddle<float, +1>(tw, r * k);
+      a[r] = mul<float>(a[r], wr);
+    }
+    dftR<float, +1, R>(a);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[t + r * NB] = a[r];
+  }
+  sync();  // the exchange buffer may be rewritten at once
+}
 
 // P3 with its accumulators in tensor memory (autotuner variant bit 8; FP32, radix 16, N = 128, 256, 512).  The last pass
 // above keeps the six product components of its 16 points per thread in registers (96 of its 254), which holds
@@ -1135,20 +1182,22 @@ __global__ void __launch_bounds__(P3TCfg<N>::THREADS, 3) k_p3_tm(const float2* _
 // (125 registers: two CTAs of 8 warps per SM, latency-bound).  Here they sit in the thread's TMEM lane (columns
 // 0-31: Phi~ as (re, im) pairs, 32-47: cells; warps w and w + 4 share a lane quarter, the latter at column 64) and are read back for every transform;
 // with a single exchange buffer (free for a two-stage transform; a three-stage
-// one syncs between a stage's reads and writes) four CTAs share an SM.  Same arithmetic as k_p1.
+// one syncs between a stage's reads and writes) three CTAs share an SM at 80 registers (measured faster than four at
+// 64).  At N <= 256, 8 of each thread's 15 last-stage twiddles also sit in its lane (columns 48-63).  Same arithmetic
+// as k_p1.
 template <int N>
 struct P1TCfg {
   static constexpr int H = N / 2, E = 16, P = N / E, TC = 256 / P, THREADS = TC * P;  // 32 / 16 / 8 columns
   static_assert(THREADS == 256, "two warps per TMEM lane quarter");
   using Lay = ColLayout<float, N, TC, E, true>;
-  static constexpr uint32_t NCOLS = 128;  // per warp group: Phi~ 0-31, cells 32-47
+  static constexpr uint32_t NCOLS = 128;  // per warp group: Phi~ 0-31, cells 32-47, 8 twiddles 48-63 (N <= 256)
   static size_t smem(int nb, int nm1) {
     return (size_t)Lay::SIZE * 8 + (size_t)N * 8 + (size_t)N * 4 + (size_t)nb * nm1 * 4 + 16;
   }
 };
 
 template <int N>
-__global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* __restrict__ phi, float2* __restrict__ Ta,
+__global__ void __launch_bounds__(P1TCfg<N>::THREADS, 3) k_p1_tm(const float2* __restrict__ phi, float2* __restrict__ Ta,
                                                                   float2* __restrict__ Tb, const int16_t* __restrict__ lut,
                                                                   const float* __restrict__ phitab, int nm1, int alpha0,
                                                                   int nb, const float2* __restrict__ tw) {
@@ -1200,6 +1249,7 @@ __global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* _
       u[r] = __int_as_float((int)lut[n0 * n0 + n1 * n1 + cc * cc]);
     }
     tmem_st16(tbase + 32, u);
+    if constexpr (N <= 256) tw8_tm_store<N>(tbase + 48, j, tw);  // 8 last-stage twiddles in columns 48-63
     tmem_wait_st();
   }
   const long fstride = (long)N * N * H;  // one field
@@ -1259,7 +1309,8 @@ __global__ void __launch_bounds__(P1TCfg<N>::THREADS, 4) k_p1_tm(const float2* _
           }
         }
       }
-      fft_pencil<float, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
+      if constexpr (N <= 256) fft_pencil_tw8_tm<N, Lay, SyncBlock>(v, j, L, tw, tbase + 48, SyncBlock());
+      else fft_pencil<float, N, E, +1, Lay, SyncBlock>(v, j, L, tw, SyncBlock());
       float2* dst = (D ? Tb : Ta) + ((long)b * nb + a) * fstride + (long)k1 * H + cc;
 #pragma unroll
       for (int r = 0; r < E; ++r) dst[(long)(j + r * P) * N * H] = v[r];
