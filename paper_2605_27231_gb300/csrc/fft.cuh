@@ -180,6 +180,7 @@ template <int N, int E> struct StockPlan {
 //   positions touched by one access phase of a warp (stride 1 or stride E) land on distinct banks.
 template <typename T, int N, bool ONE = false, int PADSH = 3> struct RowLayout {
   static constexpr bool SINGLE = ONE;                       // one buffer: a stage syncs between its reads and writes
+  static constexpr bool VEC = false;                        // first-stage values stored one by one
   static constexpr int BUF = N + (N - 1) / (1 << PADSH) + 1;  // elements per buffer
   static constexpr int SIZE = ONE ? BUF : 2 * BUF;          // elements per pencil
   cx<T>* base;
@@ -206,6 +207,7 @@ template <typename T, int N> struct RowLayoutV {
 // leave room for a second CTA per SM.
 template <typename T, int N, int TC, int E, bool ONE = false> struct ColLayout {
   static constexpr bool SINGLE = ONE;
+  static constexpr bool VEC = false;
   static constexpr int PER_PHASE = 128 / (int)sizeof(cx<T>);
   static constexpr int G0 = PER_PHASE / TC;
   // (p + p/E) mod G permutes each aligned group of G positions only while G <= E (p/E is then constant in the
@@ -295,8 +297,16 @@ __device__ __forceinline__ void fft_pencil(cx<T> (&v)[E], int j, const Lay& L, c
     cx<T>* wr = L.buf(0);
     dftR<T, DIR, E>(v);
     const int base = j * E;  // Ns = 1
+    if constexpr (Lay::VEC) {  // 16-byte pairs (RowLayoutV, FP32)
+      static_assert(E % 2 == 0 && sizeof(cx<T>) == 8, "pairs of FP32 complex values");
 #pragma unroll
-    for (int r = 0; r < E; ++r) wr[L.idx(base + r)] = v[r];
+      for (int m = 0; m < E / 2; ++m)
+        *reinterpret_cast<float4*>(wr + L.idx(base + 2 * m)) =
+            make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+    } else {
+#pragma unroll
+      for (int r = 0; r < E; ++r) wr[L.idx(base + r)] = v[r];
+    }
     sync();
     stock_stage<T, N, E, DIR, 1, Lay, Sync>(v, j, L, tw, sync);
     if constexpr (TRAIL) sync();

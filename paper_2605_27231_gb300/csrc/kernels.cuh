@@ -1390,21 +1390,44 @@ __device__ __forceinline__ void tt_amp(int n0, int n1, int n2, const double2* S,
 // is near-isotropic).  For symmetric S':
 //   |S'|^2 - 2 |S' n|^2 / |n|^2 + |n.S'.n|^2 / (2 |n|^4),
 // rational in the integer mode (one division, no square root) and the same for n and -n.
-__device__ __forceinline__ double tt_power(int n0, int n1, int n2, const double2* S) {
-  const double m0 = n0, m1 = n1, m2 = n2;
-  const double inv = 1.0 / (m0 * m0 + m1 * m1 + m2 * m2);
-  const double tx = (S[0].x + S[1].x + S[2].x) * (1.0 / 3.0), ty = (S[0].y + S[1].y + S[2].y) * (1.0 / 3.0);
-  const double2 s00 = make_double2(S[0].x - tx, S[0].y - ty), s11 = make_double2(S[1].x - tx, S[1].y - ty),
-                s22 = make_double2(S[2].x - tx, S[2].y - ty), s01 = S[3], s02 = S[4], s12 = S[5];
-  const double2 a0 = make_double2(s00.x * m0 + s01.x * m1 + s02.x * m2, s00.y * m0 + s01.y * m1 + s02.y * m2);
-  const double2 a1 = make_double2(s01.x * m0 + s11.x * m1 + s12.x * m2, s01.y * m0 + s11.y * m1 + s12.y * m2);
-  const double2 a2 = make_double2(s02.x * m0 + s12.x * m1 + s22.x * m2, s02.y * m0 + s12.y * m1 + s22.y * m2);
-  const double qx = m0 * a0.x + m1 * a1.x + m2 * a2.x, qy = m0 * a0.y + m1 * a1.y + m2 * a2.y;
-  const double ss = s00.x * s00.x + s00.y * s00.y + s11.x * s11.x + s11.y * s11.y + s22.x * s22.x + s22.y * s22.y +
-                    2.0 * (s01.x * s01.x + s01.y * s01.y + s02.x * s02.x + s02.y * s02.y + s12.x * s12.x +
-                           s12.y * s12.y);
-  const double aa = a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y + a2.x * a2.x + a2.y * a2.y;
-  return ss - 2.0 * aa * inv + 0.5 * (qx * qx + qy * qy) * inv * inv;
+// R is the arithmetic type (FP64 for the FP64 path).
+template <typename R>
+__device__ __forceinline__ R tt_power(int n0, int n1, int n2, const cx<R>* S) {
+  const R m0 = (R)n0, m1 = (R)n1, m2 = (R)n2;
+  const R inv = (R)1 / (m0 * m0 + m1 * m1 + m2 * m2);
+  const R third = (R)1 / (R)3;
+  const R tx = (S[0].x + S[1].x + S[2].x) * third, ty = (S[0].y + S[1].y + S[2].y) * third;
+  const cx<R> s00 = mk<R>(S[0].x - tx, S[0].y - ty), s11 = mk<R>(S[1].x - tx, S[1].y - ty),
+              s22 = mk<R>(S[2].x - tx, S[2].y - ty), s01 = S[3], s02 = S[4], s12 = S[5];
+  const cx<R> a0 = mk<R>(s00.x * m0 + s01.x * m1 + s02.x * m2, s00.y * m0 + s01.y * m1 + s02.y * m2);
+  const cx<R> a1 = mk<R>(s01.x * m0 + s11.x * m1 + s12.x * m2, s01.y * m0 + s11.y * m1 + s12.y * m2);
+  const cx<R> a2 = mk<R>(s02.x * m0 + s12.x * m1 + s22.x * m2, s02.y * m0 + s12.y * m1 + s22.y * m2);
+  const R qx = m0 * a0.x + m1 * a1.x + m2 * a2.x, qy = m0 * a0.y + m1 * a1.y + m2 * a2.y;
+  const R ss = s00.x * s00.x + s00.y * s00.y + s11.x * s11.x + s11.y * s11.y + s22.x * s22.x + s22.y * s22.y +
+               (R)2 * (s01.x * s01.x + s01.y * s01.y + s02.x * s02.x + s02.y * s02.y + s12.x * s12.x +
+                       s12.y * s12.y);
+  const R aa = a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y + a2.x * a2.x + a2.y * a2.y;
+  return ss - (R)2 * aa * inv + (R)0.5 * (qx * qx + qy * qy) * inv * inv;
+}
+// The same power from FP32 components, evaluated in FP32 (the FP32 path's S carries FP32 rounding already; the
+// shell sums stay FP64, and their relative error is of order eps_32 |S|^2 / power, ~1e-6).  S is first scaled by an
+// exact power of two that brings its largest component near 1, so neither the squares nor the |n|^2 factors leave
+// the FP32 range, and the factor is put back in FP64.
+__device__ __forceinline__ double tt_power_f32(int n0, int n1, int n2, const float2* S) {
+  uint32_t mb = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    mb = max(mb, __float_as_uint(S[q].x) & 0x7fffffffu);
+    mb = max(mb, __float_as_uint(S[q].y) & 0x7fffffffu);
+  }
+  if (mb == 0) return 0.0;
+  const int e = min(max((int)(mb >> 23) - 127, -126), 126);  // exponent of the largest component
+  const float sc = __uint_as_float((uint32_t)(127 - e) << 23);  // 2^-e
+  float2 T[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) T[q] = make_float2(S[q].x * sc, S[q].y * sc);
+  const double back = __longlong_as_double((long long)(1023 + 2 * e) << 52);  // 2^(2e)
+  return (double)tt_power<float>(n0, n1, n2, T) * back;
 }
 
 // F3: forward DFT along axis 0 of the six components for a tile of columns (n1 fixed, n2 = k2),
@@ -1458,12 +1481,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_f3(const cx<T>*
       const int n0 = wrapn(j + r * P, N);
       const int msq = n0 * n0 + n1 * n1 + n2 * n2;
       if (msq >= rmin && msq <= rmax) {
-        double2 S[6];
+        cx<T> St[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) S[q] = make_double2((double)X[q][r].x, (double)X[q][r].y);
-        const double pw = tt_power(n0, n1, n2, S);
+        for (int q = 0; q < 6; ++q) St[q] = X[q][r];
+        auto power = [&](int a0, int a1, int a2) -> double {
+          if constexpr (sizeof(T) == 4) return tt_power_f32(a0, a1, a2, St);
+          else return tt_power<T>(a0, a1, a2, St);
+        };
+        const double pw = power(n0, n1, n2);
         acc += pw;
         if (Xj) {
+          double2 S[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) S[q] = make_double2((double)X[q][r].x, (double)X[q][r].y);
           double2 ap, ax;
           tt_amp(n0, n1, n2, S, ap, ax);
           constexpr long NNH = (long)N * N * (H + 1);
@@ -1474,7 +1504,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_f3(const cx<T>*
         if (n2 > 0 && n2 < H) {  // the partner -n has the same projector unless n0 or n1 is a Nyquist index
           if (n0 == H || n1 == H) {
             const int p0 = (n0 == H) ? H : -n0, p1 = (n1 == H) ? H : -n1;
-            acc += tt_power(p0, p1, -n2, S);
+            acc += power(p0, p1, -n2);
           } else {
             acc += pw;
           }
