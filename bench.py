@@ -46,9 +46,9 @@ METRIC = "SIGW spectra/s at 256^3 (FP32 path; FP64 path on the same GPU under fp
 # proportion to the term-realisations of a launch, so the traffic of a bench launch is the algorithmic bytes of
 # that launch times the captured ratio.  Valid only while the kernel source is unchanged since the capture.
 NCU_TRAFFIC_256 = {
-    "p1_inv_axis0_filter": (0.0679936e9 + 1.281478e9, 0.0676e9 + 20 * 67.108864e6),  # k_p1_tm (tile in TMEM)
+    "p1_inv_axis0_filter": (0.06798208e9 + 1.281252e9, 0.0676e9 + 20 * 67.108864e6),  # k_p1_tm (tile in TMEM)
     "p2_inv_axis1": (1.073817e9 + 1.553402e9, 40 * 67.108864e6),
-    "p3_inv_axis2_product_fwd_axis2": (2.013356e9 + 0.0092119e9, 30 * 67.108864e6 + 6 * 65536 * 2 * 8),  # k_p3_tm
+    "p3_inv_axis2_product_fwd_axis2": (2.013404e9 + 0.011483904e9, 30 * 67.108864e6 + 6 * 65536 * 2 * 8),  # k_p3_tm
 }
 
 
