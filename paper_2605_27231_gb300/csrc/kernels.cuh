@@ -958,8 +958,10 @@ __device__ __forceinline__ void fft_pencil_tw8_tm(float2 (&v)[16], int j, const 
 // above keeps the six product components of its 16 points per thread in registers (96 of its 254), which holds
 // it to one CTA of 8 warps per SM.  Here they live in TMEM, in the thread's lane: s00 in columns 0-15, s12 in
 // 16-31, (s22, s11) interleaved in 32-63 and (s02, s01) interleaved in 64-95, so a thread needs ~170 registers and
-// three CTAs of 128 threads (4 warps; 16, 8 or 4 rows) share an SM.  One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the
-// stage is refilled for the next pair while the transforms run, and the other CTAs of the SM cover the copy.
+// three CTAs of 128 threads (4 warps; 16, 8 or 4 rows) share an SM.  At N <= 256 (two-stage transforms) columns
+// 96-127 hold the thread's last-stage twiddles, and the exchange rows take 16-byte first-stage stores (RowLayoutV).
+// One ring stage per CTA: the three transforms' inputs of a term pair are read into registers, the stage is
+// refilled for the next pair while the transforms run, and the other CTAs of the SM cover the copy.
 // Bounded waits, error flag and the drain before exit as in k_p3.
 template <int N>
 struct P3TCfg {
