@@ -1330,7 +1330,8 @@ __global__ void __launch_bounds__(256) k_f2(const cx<T>* __restrict__ F, cx<T>* 
                                             int nk1, const cx<T>* __restrict__ tw) {
   using SH = Shape<T, N>;
   constexpr int E = SH::ES, P = SH::PS, TC = SH::TC;
-  using Lay = ColLayout<T, N, TC, E>;
+  // one exchange buffer (a CTA runs one transform): half the shared memory of two, so more CTAs share an SM
+  using Lay = ColLayout<T, N, TC, E, true>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int c = threadIdx.x % TC, j = threadIdx.x / TC;
   const Lay L{reinterpret_cast<cx<T>*>(smraw), c};

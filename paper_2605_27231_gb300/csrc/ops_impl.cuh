@@ -167,7 +167,7 @@ struct OpsT {
   template <int N>
   static cudaError_t f2_n(const void* F, void* F2, int n_c, int batch, const void* tw, cudaStream_t st) {
     using SH = Shape<T, N>;
-    const size_t sm = col_bytes<N, SH::TC, SH::ES>();
+    const size_t sm = (size_t)ColLayout<T, N, SH::TC, SH::ES, true>::SIZE * sizeof(C);  // single exchange buffer
     auto k = k_f2<T, N>;
     SIGW_CHECK_LAUNCH(allow_smem(k, sm));
     int lo, nk1;
